@@ -1,0 +1,602 @@
+/*
+ * Gradient-SDF CPU oracle -- TEST INFRASTRUCTURE ONLY (see gsdf_oracle.h).
+ *
+ * Plain restatement of the paper's definitions:
+ *   Sec. 3.1, Eq. (sdf_update)       psi <- (W psi + w d)/(W + w),  W <- W + w
+ *   Sec. 3.2, Eq. (gradient_update)  g <- g + w n,  ghat = g/|g|
+ *   Sec. 4.1, Eq. (tracking)         E(R,t) = sum_k w_k d_S(R p_k + t)^2
+ *   Sec. 4.1, Eq. (taylor)           d(p) = psi_j* + (p - v_j*)^T ghat_j*,  grad d = ghat_j*,
+ *                                    j* = nearest grid voxel = round(p / v_s)
+ *   Sec. 5.1                         Gauss-Newton, Cholesky solve of the normal equations
+ *   Sec. 5.3                         pixel-driven integration: each pixel updates the voxels on
+ *                                    its viewing ray within the truncation band; linear weight;
+ *                                    depth cutoff 3.5 m; normals with angle to the ray < 75 deg.
+ * Readings where the paper is silent (all stated in the header comments of each function):
+ *   - inside-positive sign (Sec. 3.1): d(v) = z_v - D(u), z_v the camera-space depth of the voxel
+ *     centre; normals oriented away from the camera;
+ *   - ray sampling: samples z_k = D + (k - K) v_s/2, k = 0..2K, K = ceil(T / (v_s/2)), each sample
+ *     rounded to its voxel; consecutive duplicates collapsed (a ray visits a voxel once);
+ *   - linear weight: w = 1 for d <= eps, (T - d)/(T - eps) for eps < d <= T, none for |d| > T;
+ *   - normals: cross product of central differences of back-projected neighbours;
+ *   - tracking weight w_k: Huber with threshold delta, recomputed each Gauss-Newton step;
+ *     a pixel whose nearest voxel is missing, has W = 0 or g = 0 is skipped;
+ *   - pose update: left-multiplicative, T <- exp(xi^) T with xi = (omega, upsilon) = -H^-1 b.
+ */
+#include "gsdf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------------ */
+/* per-voxel hash map (one voxel per entry, Sec. 5.1)                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t m[3];
+    int32_t used;
+    double psi;
+    double g[3];
+    double w;
+} orc_entry;
+
+struct orc_map {
+    orc_params prm;
+    int dense;
+    int dims[3];
+    int origin[3];
+    orc_entry* tab;
+    size_t cap; /* power of two */
+    size_t count;
+};
+
+static uint64_t orc_hash(const int32_t m[3]) {
+    uint64_t k = ((uint64_t)(uint32_t)m[0] * 0x9E3779B97F4A7C15ull) ^
+                 ((uint64_t)(uint32_t)m[1] * 0xC2B2AE3D27D4EB4Full) ^
+                 ((uint64_t)(uint32_t)m[2] * 0x165667B19E3779F9ull);
+    k ^= k >> 33;
+    k *= 0xFF51AFD7ED558CCDull;
+    k ^= k >> 33;
+    return k;
+}
+
+static orc_entry* orc_find(const orc_map* map, const int32_t m[3]) {
+    size_t mask = map->cap - 1;
+    size_t i = (size_t)orc_hash(m) & mask;
+    for (;;) {
+        orc_entry* e = &map->tab[i];
+        if (!e->used) return NULL;
+        if (e->m[0] == m[0] && e->m[1] == m[1] && e->m[2] == m[2]) return e;
+        i = (i + 1) & mask;
+    }
+}
+
+static int orc_grow(orc_map* map) {
+    size_t ncap = map->cap * 2;
+    orc_entry* nt = (orc_entry*)calloc(ncap, sizeof(orc_entry));
+    if (!nt) return -1;
+    for (size_t j = 0; j < map->cap; ++j) {
+        if (!map->tab[j].used) continue;
+        size_t i = (size_t)orc_hash(map->tab[j].m) & (ncap - 1);
+        while (nt[i].used) i = (i + 1) & (ncap - 1);
+        nt[i] = map->tab[j];
+    }
+    free(map->tab);
+    map->tab = nt;
+    map->cap = ncap;
+    return 0;
+}
+
+/* find or insert a zero voxel (psi = 0, g = 0, W = 0) */
+static orc_entry* orc_get(orc_map* map, const int32_t m[3]) {
+    orc_entry* e = orc_find(map, m);
+    if (e) return e;
+    if (2 * (map->count + 1) > map->cap && orc_grow(map) != 0) return NULL;
+    size_t mask = map->cap - 1;
+    size_t i = (size_t)orc_hash(m) & mask;
+    while (map->tab[i].used) i = (i + 1) & mask;
+    e = &map->tab[i];
+    memset(e, 0, sizeof(*e));
+    e->m[0] = m[0];
+    e->m[1] = m[1];
+    e->m[2] = m[2];
+    e->used = 1;
+    map->count++;
+    return e;
+}
+
+orc_map* orc_map_new(const orc_params* prm) {
+    orc_map* map = (orc_map*)calloc(1, sizeof(orc_map));
+    if (!map) return NULL;
+    map->prm = *prm;
+    map->cap = 1024;
+    map->tab = (orc_entry*)calloc(map->cap, sizeof(orc_entry));
+    if (!map->tab) {
+        free(map);
+        return NULL;
+    }
+    return map;
+}
+
+orc_map* orc_map_new_dense(const orc_params* prm, const int dims[3], const int origin[3]) {
+    orc_map* map = orc_map_new(prm);
+    if (!map) return NULL;
+    map->dense = 1;
+    for (int i = 0; i < 3; ++i) {
+        map->dims[i] = dims[i];
+        map->origin[i] = origin[i];
+    }
+    return map;
+}
+
+void orc_map_free(orc_map* map) {
+    if (!map) return;
+    free(map->tab);
+    free(map);
+}
+
+size_t orc_map_count(const orc_map* map) {
+    size_t n = 0;
+    for (size_t i = 0; i < map->cap; ++i) n += map->tab[i].used && map->tab[i].w > 0.0;
+    return n;
+}
+
+static int orc_in_dense(const orc_map* map, const int32_t m[3]) {
+    if (!map->dense) return 1;
+    for (int i = 0; i < 3; ++i)
+        if (m[i] < map->origin[i] || m[i] >= map->origin[i] + map->dims[i]) return 0;
+    return 1;
+}
+
+int orc_map_set_dense(orc_map* map, const float* psi, const float* g, const float* w) {
+    if (!map->dense) return -1;
+    size_t idx = 0;
+    for (int z = 0; z < map->dims[2]; ++z)
+        for (int y = 0; y < map->dims[1]; ++y)
+            for (int x = 0; x < map->dims[0]; ++x, ++idx) {
+                if (!(w[idx] > 0.0f)) continue;
+                int32_t m[3] = {map->origin[0] + x, map->origin[1] + y, map->origin[2] + z};
+                orc_entry* e = orc_get(map, m);
+                if (!e) return -1;
+                e->psi = psi[idx];
+                e->g[0] = g[3 * idx + 0];
+                e->g[1] = g[3 * idx + 1];
+                e->g[2] = g[3 * idx + 2];
+                e->w = w[idx];
+            }
+    return 0;
+}
+
+void orc_block_of(const int32_t m[3], int32_t b[3], int32_t local[3]) {
+    for (int i = 0; i < 3; ++i) {
+        int32_t q = m[i] >= 0 ? m[i] / 8 : -((-m[i] + 7) / 8); /* floor(m / 8) */
+        b[i] = q;
+        local[i] = m[i] - 8 * q;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* FP32 index path                                                                             */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+    float R[9], t[3];      /* camera -> world, rounded once from FP64 */
+    float RT[9], tinv[3];  /* world -> camera: R^T and -R^T t (FP64, then rounded once) */
+} orc_pose32;
+
+static void orc_round_pose(const double T[16], orc_pose32* q) {
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            q->R[3 * i + j] = (float)T[4 * i + j];
+            q->RT[3 * i + j] = (float)T[4 * j + i];
+        }
+        q->t[i] = (float)T[4 * i + 3];
+        double s = T[0 * 4 + i] * T[3];
+        s = s + T[1 * 4 + i] * T[7];
+        s = s + T[2 * 4 + i] * T[11];
+        q->tinv[i] = (float)(-s);
+    }
+}
+
+/* P = ((R_i0 p0 + R_i1 p1) + R_i2 p2) + t_i, each operation rounded to FP32 */
+static void orc_xform32(const float R[9], const float t[3], const float p[3], float P[3]) {
+    for (int i = 0; i < 3; ++i) {
+        float a = R[3 * i + 0] * p[0];
+        float b = R[3 * i + 1] * p[1];
+        float c = R[3 * i + 2] * p[2];
+        float s = a + b;
+        s = s + c;
+        P[i] = s + t[i];
+    }
+}
+
+/* j* of Eq. (taylor): nearest grid voxel, m = floor(P / v_s + 1/2) with 1/v_s rounded to FP32 */
+static void orc_round_voxel(const float P[3], float inv_vs, int32_t m[3]) {
+    for (int i = 0; i < 3; ++i) {
+        float s = P[i] * inv_vs;
+        s = s + 0.5f;
+        m[i] = (int32_t)floorf(s);
+    }
+}
+
+static int orc_depth_ok(float D, float dmax) { return D > 0.0f && D <= dmax; }
+
+typedef struct {
+    float ifx, ify, inv_vs;
+} orc_recip;
+
+static orc_recip orc_recips(const orc_intrinsics* K, float vs) {
+    orc_recip r;
+    r.ifx = (float)(1.0 / (double)K->fx);
+    r.ify = (float)(1.0 / (double)K->fy);
+    r.inv_vs = (float)(1.0 / (double)vs);
+    return r;
+}
+
+/* back-projection of pixel (u, v) at depth z: z * ((u - cx)/fx, (v - cy)/fy, 1) */
+static void orc_backproject(const orc_intrinsics* K, const orc_recip* rc, int u, int v, float z, float p[3]) {
+    float xn = ((float)u - K->cx) * rc->ifx;
+    float yn = ((float)v - K->cy) * rc->ify;
+    p[0] = z * xn;
+    p[1] = z * yn;
+    p[2] = z;
+}
+
+void orc_pixel_point(const orc_intrinsics* K, const double T_wc[16], int u, int v, float D,
+                     float P_out[3], int32_t m_out[3], float voxel_size) {
+    orc_pose32 q;
+    orc_round_pose(T_wc, &q);
+    orc_recip rc = orc_recips(K, voxel_size);
+    float p[3];
+    orc_backproject(K, &rc, u, v, D, p);
+    orc_xform32(q.R, q.t, p, P_out);
+    orc_round_voxel(P_out, rc.inv_vs, m_out);
+}
+
+static float orc_dot32(const float a[3], const float b[3]) {
+    float s = a[0] * b[0];
+    s = s + a[1] * b[1];
+    s = s + a[2] * b[2];
+    return s;
+}
+
+/* Normal of pixel (u, v), Sec. 5.3 (75 degree filter).  Reading: central differences of the
+ * back-projected 4-neighbours, n = (p_r - p_l) x (p_d - p_u), normalised, oriented so that
+ * n . p > 0 (away from the camera, i.e. along the inside-positive SDF gradient).  Rejected at the
+ * image border, if a neighbour is invalid or differs from the centre depth by more than T, if
+ * the cross product vanishes, or if n . p / |p| < cos(75 deg). */
+int orc_normal(const float* depth, const orc_intrinsics* K, const orc_params* prm, int u, int v,
+               float n_out[3]) {
+    const int W = K->width, H = K->height;
+    if (u < 1 || u >= W - 1 || v < 1 || v >= H - 1) return 0;
+    const float D = depth[(size_t)v * W + u];
+    if (!orc_depth_ok(D, K->depth_max)) return 0;
+    const float Dl = depth[(size_t)v * W + u - 1], Dr = depth[(size_t)v * W + u + 1];
+    const float Du = depth[(size_t)(v - 1) * W + u], Dd = depth[(size_t)(v + 1) * W + u];
+    const float nb[4] = {Dl, Dr, Du, Dd};
+    for (int i = 0; i < 4; ++i) {
+        if (!orc_depth_ok(nb[i], K->depth_max)) return 0;
+        float diff = nb[i] - D;
+        if (diff > prm->truncation || diff < -prm->truncation) return 0;
+    }
+    orc_recip rc = orc_recips(K, prm->voxel_size);
+    float pl[3], pr[3], pu[3], pd[3], p[3];
+    orc_backproject(K, &rc, u - 1, v, Dl, pl);
+    orc_backproject(K, &rc, u + 1, v, Dr, pr);
+    orc_backproject(K, &rc, u, v - 1, Du, pu);
+    orc_backproject(K, &rc, u, v + 1, Dd, pd);
+    orc_backproject(K, &rc, u, v, D, p);
+    float a[3] = {pr[0] - pl[0], pr[1] - pl[1], pr[2] - pl[2]};
+    float b[3] = {pd[0] - pu[0], pd[1] - pu[1], pd[2] - pu[2]};
+    float n[3];
+    n[0] = a[1] * b[2] - a[2] * b[1];
+    n[1] = a[2] * b[0] - a[0] * b[2];
+    n[2] = a[0] * b[1] - a[1] * b[0];
+    float nn = orc_dot32(n, n);
+    if (!(nn > 0.0f)) return 0;
+    float s = sqrtf(nn);
+    n[0] = n[0] / s;
+    n[1] = n[1] / s;
+    n[2] = n[2] / s;
+    float dp = orc_dot32(n, p);
+    if (dp < 0.0f) {
+        n[0] = -n[0];
+        n[1] = -n[1];
+        n[2] = -n[2];
+        dp = -dp;
+    }
+    float c = dp / sqrtf(orc_dot32(p, p));
+    if (!(c >= prm->cos_max_angle)) return 0;
+    n_out[0] = n[0];
+    n_out[1] = n[1];
+    n_out[2] = n[2];
+    return 1;
+}
+
+/* half-width K of the ray band in samples of v_s / 2: ceil(T / (v_s/2)), in FP64 with a 1e-6
+ * guard so that T = 5 v_s gives exactly 10 */
+static int orc_band_half(float vs, float T) {
+    double h = (double)(0.5f * vs);
+    return (int)ceil((double)T / h - 1e-6);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* integration: Eqs. (sdf_update), (gradient_update), pixel-driven as in Sec. 5.3             */
+/* ------------------------------------------------------------------------------------------ */
+
+int orc_integrate(orc_map* map, const float* depth, const orc_intrinsics* K, const double T_wc[16],
+                  orc_integrate_stats* st) {
+    const orc_params* prm = &map->prm;
+    orc_pose32 q;
+    orc_round_pose(T_wc, &q);
+    orc_recip rc = orc_recips(K, prm->voxel_size);
+    const float vs = prm->voxel_size, T = prm->truncation, eps = prm->weight_eps;
+    const float h = 0.5f * vs;
+    const int Kb = orc_band_half(vs, T);
+    int64_t n_rays = 0, n_visits = 0;
+    for (int v = 0; v < K->height; ++v) {
+        for (int u = 0; u < K->width; ++u) {
+            const float D = depth[(size_t)v * K->width + u];
+            float n[3];
+            if (!orc_normal(depth, K, prm, u, v, n)) continue; /* includes the depth test */
+            n_rays++;
+            /* world normal n_w = R n (values in FP64 from the FP32 rotation) */
+            double nw[3];
+            for (int i = 0; i < 3; ++i)
+                nw[i] = (double)q.R[3 * i] * n[0] + (double)q.R[3 * i + 1] * n[1] + (double)q.R[3 * i + 2] * n[2];
+            int32_t prev[3] = {0, 0, 0};
+            int have_prev = 0;
+            for (int k = 0; k <= 2 * Kb; ++k) {
+                float step = (float)(k - Kb) * h;
+                float z = D + step;
+                float p[3], P[3];
+                orc_backproject(K, &rc, u, v, z, p);
+                orc_xform32(q.R, q.t, p, P);
+                int32_t m[3];
+                orc_round_voxel(P, rc.inv_vs, m);
+                if (have_prev && m[0] == prev[0] && m[1] == prev[1] && m[2] == prev[2]) continue;
+                prev[0] = m[0];
+                prev[1] = m[1];
+                prev[2] = m[2];
+                have_prev = 1;
+                /* distance estimate d(v) = z_v - D (projective, inside-positive) */
+                float vc[3] = {(float)m[0] * vs, (float)m[1] * vs, (float)m[2] * vs};
+                float zv = q.RT[6] * vc[0];
+                zv = zv + q.RT[7] * vc[1];
+                zv = zv + q.RT[8] * vc[2];
+                zv = zv + q.tinv[2];
+                float d = zv - D;
+                if (d > T || d < -T) continue;
+                if (!orc_in_dense(map, m)) continue;
+                double w = (d <= eps) ? 1.0 : ((double)T - (double)d) / ((double)T - (double)eps);
+                if (!(w > 0.0)) continue;
+                orc_entry* e = orc_get(map, m);
+                if (!e) return -1;
+                /* Eq. (sdf_update) and Eq. (gradient_update), applied in ray order */
+                e->psi = (e->w * e->psi + w * (double)d) / (e->w + w);
+                e->w = e->w + w;
+                e->g[0] += w * nw[0];
+                e->g[1] += w * nw[1];
+                e->g[2] += w * nw[2];
+                n_visits++;
+            }
+        }
+    }
+    if (st) {
+        st->n_rays = n_rays;
+        st->n_visits = n_visits;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* tracking: Eq. (tracking) with the Taylor model Eq. (taylor)                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+int orc_taylor(const orc_map* map, const double P[3], const int32_t m[3], double* r, double ghat[3]) {
+    const orc_entry* e = orc_find(map, m);
+    if (!e || !(e->w > 0.0)) return 1;
+    double gn = sqrt(e->g[0] * e->g[0] + e->g[1] * e->g[1] + e->g[2] * e->g[2]);
+    if (!(gn > 0.0)) return 1;
+    const double vs = (double)map->prm.voxel_size;
+    double s = e->psi;
+    for (int i = 0; i < 3; ++i) {
+        ghat[i] = e->g[i] / gn;
+        s += ghat[i] * (P[i] - vs * (double)m[i]);
+    }
+    *r = s;
+    return 0;
+}
+
+int orc_track_reduce(const orc_map* map, const float* depth, const orc_intrinsics* K,
+                     const double T_wc[16], orc_track_stats* st) {
+    const orc_params* prm = &map->prm;
+    orc_pose32 q;
+    orc_round_pose(T_wc, &q);
+    orc_recip rc = orc_recips(K, prm->voxel_size);
+    const double delta = prm->huber_delta;
+    double A[6][6] = {{0}};
+    double b[6] = {0};
+    double E = 0.0;
+    int64_t n = 0, nh = 0;
+    for (int v = 0; v < K->height; ++v) {
+        for (int u = 0; u < K->width; ++u) {
+            const float D = depth[(size_t)v * K->width + u];
+            if (!orc_depth_ok(D, K->depth_max)) continue;
+            float p[3], Pf[3];
+            int32_t m[3];
+            orc_backproject(K, &rc, u, v, D, p);
+            orc_xform32(q.R, q.t, p, Pf);
+            orc_round_voxel(Pf, rc.inv_vs, m);
+            double P[3] = {Pf[0], Pf[1], Pf[2]}, gh[3], r;
+            if (orc_taylor(map, P, m, &r, gh) != 0) continue;
+            /* J = d r / d xi for T <- exp(xi^) T, xi = (omega, upsilon): (P x ghat, ghat) */
+            double J[6] = {P[1] * gh[2] - P[2] * gh[1], P[2] * gh[0] - P[0] * gh[2],
+                           P[0] * gh[1] - P[1] * gh[0], gh[0], gh[1], gh[2]};
+            double ar = fabs(r);
+            double w = ar <= delta ? 1.0 : delta / ar;
+            if (ar > delta) nh++;
+            for (int i = 0; i < 6; ++i) {
+                for (int j = i; j < 6; ++j) A[i][j] += w * J[i] * J[j];
+                b[i] += w * J[i] * r;
+            }
+            E += w * r * r;
+            n++;
+        }
+    }
+    int idx = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) st->H[idx++] = A[i][j];
+    for (int i = 0; i < 6; ++i) st->b[i] = b[i];
+    st->energy = E;
+    st->n_valid = n;
+    st->n_huber = nh;
+    st->status = 0;
+    for (int i = 0; i < 6; ++i) st->xi[i] = 0.0;
+    return 0;
+}
+
+/* Cholesky solve of (H + lambda I) xi = -b (Sec. 5.1).  lambda = damping * mean(diag H).
+ * Degenerate (returns 1, xi = 0) if fewer than 6 residuals or a pivot <= 1e-12 max diag. */
+int orc_solve6(const double H21[21], const double b[6], double damping, int64_t n_valid, double xi[6]) {
+    double A[6][6];
+    int idx = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+            A[i][j] = H21[idx];
+            A[j][i] = H21[idx];
+            idx++;
+        }
+    for (int i = 0; i < 6; ++i) xi[i] = 0.0;
+    if (damping > 0.0) {
+        double tr = 0.0;
+        for (int i = 0; i < 6; ++i) tr += A[i][i];
+        double lam = damping * tr / 6.0;
+        for (int i = 0; i < 6; ++i) A[i][i] += lam;
+    }
+    if (n_valid < 6) return 1;
+    double maxd = 0.0;
+    for (int i = 0; i < 6; ++i) maxd = A[i][i] > maxd ? A[i][i] : maxd;
+    if (!(maxd > 0.0)) return 1;
+    double L[6][6] = {{0}};
+    for (int j = 0; j < 6; ++j) {
+        double s = A[j][j];
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 1e-12 * maxd)) return 1;
+        L[j][j] = sqrt(s);
+        for (int i = j + 1; i < 6; ++i) {
+            double t = A[i][j];
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double t = -b[i];
+        for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+        y[i] = t / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double t = y[i];
+        for (int k = i + 1; k < 6; ++k) t -= L[k][i] * xi[k];
+        xi[i] = t / L[i][i];
+    }
+    return 0;
+}
+
+/* SE(3) exponential of xi = (omega, upsilon): R by Rodrigues, t = V upsilon with
+ * V = I + (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2 (series for small th) */
+void orc_se3_exp(const double xi[6], double T[16]) {
+    const double* w = xi;
+    const double* u = xi + 3;
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double A, B, C;
+    if (th < 1e-4) {
+        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / th2;
+        C = (th - sin(th)) / (th2 * th);
+    }
+    double Wx[3][3] = {{0, -w[2], w[1]}, {w[2], 0, -w[0]}, {-w[1], w[0], 0}};
+    double W2[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += Wx[i][k] * Wx[k][j];
+            W2[i][j] = s;
+        }
+    double R[3][3], V[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double I = (i == j) ? 1.0 : 0.0;
+            R[i][j] = I + A * Wx[i][j] + B * W2[i][j];
+            V[i][j] = I + B * Wx[i][j] + C * W2[i][j];
+        }
+    memset(T, 0, 16 * sizeof(double));
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) T[4 * i + j] = R[i][j];
+        T[4 * i + 3] = V[i][0] * u[0] + V[i][1] * u[1] + V[i][2] * u[2];
+    }
+    T[15] = 1.0;
+}
+
+int orc_track_step(const orc_map* map, const float* depth, const orc_intrinsics* K, double T_wc[16],
+                   orc_track_stats* st) {
+    orc_track_reduce(map, depth, K, T_wc, st);
+    double xi[6];
+    int bad = orc_solve6(st->H, st->b, map->prm.damping, st->n_valid, xi);
+    st->status = bad;
+    for (int i = 0; i < 6; ++i) st->xi[i] = xi[i];
+    if (bad) return 0;
+    double dT[16], Tn[16];
+    orc_se3_exp(xi, dT);
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k) s += dT[4 * i + k] * T_wc[4 * k + j];
+            Tn[4 * i + j] = s;
+        }
+    memcpy(T_wc, Tn, sizeof(Tn));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* extraction                                                                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+static int orc_cmp_voxel(const void* pa, const void* pb) {
+    const orc_voxel_out* a = (const orc_voxel_out*)pa;
+    const orc_voxel_out* b = (const orc_voxel_out*)pb;
+    for (int i = 0; i < 3; ++i) {
+        if (a->m[i] < b->m[i]) return -1;
+        if (a->m[i] > b->m[i]) return 1;
+    }
+    return 0;
+}
+
+size_t orc_extract(const orc_map* map, orc_voxel_out* out, size_t cap) {
+    size_t n = 0;
+    for (size_t i = 0; i < map->cap; ++i) {
+        const orc_entry* e = &map->tab[i];
+        if (!e->used || !(e->w > 0.0)) continue;
+        if (n < cap) {
+            orc_voxel_out* o = &out[n];
+            o->m[0] = e->m[0];
+            o->m[1] = e->m[1];
+            o->m[2] = e->m[2];
+            o->psi = e->psi;
+            o->g[0] = e->g[0];
+            o->g[1] = e->g[1];
+            o->g[2] = e->g[2];
+            o->w = e->w;
+        }
+        n++;
+    }
+    size_t k = n < cap ? n : cap;
+    qsort(out, k, sizeof(orc_voxel_out), orc_cmp_voxel);
+    return n;
+}

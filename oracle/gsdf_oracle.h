@@ -1,0 +1,107 @@
+/*
+ * Gradient-SDF CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded C restatement of the method's definitions, used to check the
+ * CUDA library.  Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+ * load it; the product path never does.  It shares no code with the CUDA library.
+ *
+ * Numerics: every value (psi, g, W, residuals, Jacobians, normal equations, Cholesky, SE(3)
+ * exponential) is FP64.  Every *discrete decision* (which pixel is valid, which voxel a point
+ * rounds to, whether a normal passes the 75 degree test, whether a voxel lies inside the
+ * truncation band) is taken on an explicit FP32 "index path" whose operations and their order are
+ * fixed, so that any implementation doing the same correctly rounded FP32 operations takes the
+ * same decisions bit for bit.  Compile with -ffp-contract=off and without -ffast-math.
+ *
+ * Map storage follows Sec. 5.1 of the paper: one hash-map entry per voxel holding
+ * (psi, g, W).  A "dense" map is the same storage restricted to a box of voxel coordinates.
+ */
+#ifndef GSDF_ORACLE_H
+#define GSDF_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_map orc_map;
+
+/* camera intrinsics; pixel (u, v) has integer coordinates; depth_max is the 3.5 m cutoff of Sec. 5.3 */
+typedef struct {
+    float fx, fy, cx, cy;
+    int width, height;
+    float depth_max;
+} orc_intrinsics;
+
+/* method parameters (Sec. 5.3): voxel size v_s, truncation T, linear-weight knee eps,
+ * Huber threshold delta, cos of the maximum normal/ray angle (75 degrees) */
+typedef struct {
+    float voxel_size;
+    float truncation;
+    float weight_eps;
+    float huber_delta;
+    float cos_max_angle;
+    double damping; /* relative Levenberg-Marquardt damping, 0 = plain Gauss-Newton */
+} orc_params;
+
+typedef struct {
+    int32_t m[3];
+    double psi;
+    double g[3];
+    double w;
+} orc_voxel_out;
+
+typedef struct {
+    double H[21]; /* upper triangle of sum w J J^T, row-major */
+    double b[6];  /* sum w J r */
+    double energy;
+    int64_t n_valid;
+    int64_t n_huber;
+    int status;   /* 0 ok, 1 degenerate (pose unchanged) */
+    double xi[6]; /* applied increment (omega, upsilon) */
+} orc_track_stats;
+
+typedef struct {
+    int64_t n_rays;   /* pixels that passed the depth and normal tests */
+    int64_t n_visits; /* ray-voxel updates with w > 0 */
+} orc_integrate_stats;
+
+orc_map* orc_map_new(const orc_params* prm);
+/* dense box [origin, origin + dims); integration outside it is skipped */
+orc_map* orc_map_new_dense(const orc_params* prm, const int dims[3], const int origin[3]);
+void orc_map_free(orc_map* map);
+size_t orc_map_count(const orc_map* map);
+/* set voxel values directly (analytic maps); psi/g/w arrays are x-fastest over dims */
+int orc_map_set_dense(orc_map* map, const float* psi, const float* g, const float* w);
+
+/* Eqs. sdf_update / gradient_update, pixel-driven as in Sec. 5.3 */
+int orc_integrate(orc_map* map, const float* depth, const orc_intrinsics* K, const double T_wc[16],
+                  orc_integrate_stats* st);
+/* normal equations of Eq. (tracking) with the Taylor model Eq. (taylor) at pose T_wc */
+int orc_track_reduce(const orc_map* map, const float* depth, const orc_intrinsics* K,
+                     const double T_wc[16], orc_track_stats* st);
+/* one Gauss-Newton step: reduce, Cholesky solve, left-multiplicative SE(3) update */
+int orc_track_step(const orc_map* map, const float* depth, const orc_intrinsics* K, double T_wc[16],
+                   orc_track_stats* st);
+
+/* pieces exposed for the pins */
+int orc_solve6(const double H21[21], const double b[6], double damping, int64_t n_valid, double xi[6]);
+void orc_se3_exp(const double xi[6], double T[16]);
+/* Taylor model at world point P using voxel m: returns 0 if usable, fills r and ghat */
+int orc_taylor(const orc_map* map, const double P[3], const int32_t m[3], double* r, double ghat[3]);
+/* FP32 index path: world point of pixel (u, v) at depth D and its rounded voxel coordinate */
+void orc_pixel_point(const orc_intrinsics* K, const double T_wc[16], int u, int v, float D,
+                     float P_out[3], int32_t m_out[3], float voxel_size);
+/* FP32 normal of pixel (u, v) in camera coordinates; returns 1 if it passes every test */
+int orc_normal(const float* depth, const orc_intrinsics* K, const orc_params* prm, int u, int v,
+               float n_out[3]);
+/* voxels with W > 0 sorted by (x, y, z); returns the number written (<= cap) */
+size_t orc_extract(const orc_map* map, orc_voxel_out* out, size_t cap);
+/* block coordinate (floor division by 8) and local index of a voxel coordinate */
+void orc_block_of(const int32_t m[3], int32_t b[3], int32_t local[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

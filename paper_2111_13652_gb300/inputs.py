@@ -1,0 +1,393 @@
+"""Seeded synthetic inputs: analytic scenes, an FP64 ray-caster, camera trajectories, depth noise.
+
+This module produces *inputs only*: depth images, camera poses and (for the dense sphere case)
+the analytic grid values that the method is then run on.  It holds none of the method's
+arithmetic (no back-projection into the map, no fusion, no tracking), so the CUDA path and the
+CPU oracle can both consume it without sharing method code.
+
+Conventions (stated once, used everywhere):
+  * camera frame: x right, y down, z forward; pixel (u, v) looks along (u - cx)/fx, (v - cy)/fy, 1;
+  * a pose T_wc is a 4x4 row-major FP64 matrix mapping camera points to world points, P = R p + t;
+  * depth is z-depth in metres (FP32), 0 marks "no measurement";
+  * signed distances are inside-positive (negative in free space), matching Sec. 3.1 of the paper.
+
+The synthetic workloads take the shapes of the paper's RGB-D data (Sec. 5.3: 640x480 frames,
+3.5 m depth cutoff, 1-2 cm voxels, truncation 5 voxels); the TUM/Redwood sequences themselves
+are not used.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------------------------
+# small pose helpers (input construction only)
+# --------------------------------------------------------------------------------------------
+
+
+def look_at(position, target, up=(0.0, 0.0, 1.0), roll=0.0) -> np.ndarray:
+    """Camera-to-world pose at `position` whose optical axis (+z) points at `target`."""
+    c = np.asarray(position, np.float64)
+    z = np.asarray(target, np.float64) - c
+    z /= np.linalg.norm(z)
+    x = np.cross(z, np.asarray(up, np.float64))
+    if np.linalg.norm(x) < 1e-9:  # looking straight up/down: pick any horizontal x
+        x = np.cross(z, np.array([1.0, 0.0, 0.0]))
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z], axis=1)
+    if roll != 0.0:
+        R = R @ axis_angle(np.array([0.0, 0.0, 1.0]), roll)
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = c
+    return T
+
+
+def axis_angle(axis, angle) -> np.ndarray:
+    """Rotation matrix about a unit axis (input construction; Rodrigues' formula)."""
+    a = np.asarray(axis, np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
+
+
+def perturb_pose(T: np.ndarray, rng: np.random.Generator, angle_deg=5.0, trans_m=0.05) -> np.ndarray:
+    """Left-multiply T by a rotation of `angle_deg` about a random axis and a random translation."""
+    axis = rng.normal(size=3)
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    dT = np.eye(4)
+    dT[:3, :3] = axis_angle(axis, math.radians(angle_deg))
+    dT[:3, 3] = trans_m * d
+    return dT @ T
+
+
+# --------------------------------------------------------------------------------------------
+# camera
+# --------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass(frozen=True)
+class Camera:
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+    depth_max: float = 3.5
+
+    def ray_dirs_cam(self) -> np.ndarray:
+        """(H*W, 3) FP64 camera-frame ray directions with unit z (so ray parameter = z-depth)."""
+        u = np.arange(self.width, dtype=np.float64)
+        v = np.arange(self.height, dtype=np.float64)
+        uu, vv = np.meshgrid(u, v)
+        d = np.stack([(uu - self.cx) / self.fx, (vv - self.cy) / self.fy, np.ones_like(uu)], axis=-1)
+        return d.reshape(-1, 3)
+
+
+KINECT_640 = Camera(525.0, 525.0, 319.5, 239.5, 640, 480, 3.5)
+TINY_160 = Camera(140.0, 140.0, 80.0, 60.0, 160, 120, 3.5)
+
+
+# --------------------------------------------------------------------------------------------
+# analytic scenes and ray casting (FP64)
+# --------------------------------------------------------------------------------------------
+
+
+def _ray_sphere(o, d, c, r):
+    """Smallest positive ray parameter hitting sphere (c, r) from outside; inf if none."""
+    oc = o - c
+    a = np.einsum("ij,ij->i", d, d)
+    b = 2.0 * (d @ oc)
+    cc = float(oc @ oc) - r * r
+    disc = b * b - 4 * a * cc
+    t = np.full(d.shape[0], np.inf)
+    ok = np.nonzero(disc >= 0)[0]
+    if ok.size == 0:
+        return t
+    sq = np.sqrt(disc[ok])
+    t0 = (-b[ok] - sq) / (2 * a[ok])
+    t1 = (-b[ok] + sq) / (2 * a[ok])
+    t[ok] = np.where(t0 > 1e-9, t0, np.where(t1 > 1e-9, t1, np.inf))
+    return t
+
+
+def _ray_box(o, d, lo, hi):
+    """Entry parameter into the solid axis-aligned box [lo, hi] (camera outside); inf if missed."""
+    t = np.full(d.shape[0], np.inf)
+    c = 0.5 * (lo + hi)
+    cand = np.isfinite(_ray_sphere(o, d, c, float(np.linalg.norm(hi - c)) + 1e-6))
+    if not np.any(cand):
+        return t
+    dc = d[cand]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / dc
+        t1 = (lo - o) * inv
+        t2 = (hi - o) * inv
+    t1 = np.where(np.isnan(t1), -np.inf, t1)
+    t2 = np.where(np.isnan(t2), np.inf, t2)
+    tmin = np.max(np.minimum(t1, t2), axis=1)
+    tmax = np.min(np.maximum(t1, t2), axis=1)
+    hit = (tmax >= tmin) & (tmax > 1e-9)
+    t[cand] = np.where(hit, np.where(tmin > 1e-9, tmin, tmax), np.inf)
+    return t
+
+
+def _ray_room_exit(o, d, lo, hi):
+    """Ray parameter where a ray starting inside the box [lo, hi] leaves it (hits a wall)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        t_hi = (hi - o) * inv
+        t_lo = (lo - o) * inv
+    t_exit = np.where(d > 0, t_hi, np.where(d < 0, t_lo, np.inf))
+    return np.min(t_exit, axis=1)
+
+
+@dataclasses.dataclass
+class SphereScene:
+    center: np.ndarray
+    radius: float
+
+    def raycast(self, o, d):
+        return _ray_sphere(o, d, self.center, self.radius)
+
+    def sdf(self, x):
+        """Inside-positive signed distance r - |x - c| and its gradient -(x - c)/|x - c|."""
+        rel = x - self.center
+        n = np.linalg.norm(rel, axis=-1)
+        psi = self.radius - n
+        with np.errstate(invalid="ignore", divide="ignore"):
+            g = -rel / n[..., None]
+        return psi, g
+
+
+@dataclasses.dataclass
+class RoomScene:
+    lo: np.ndarray  # room interior bounds (walls face inward)
+    hi: np.ndarray
+    spheres: list  # [(center(3,), r)]
+    boxes: list  # [(lo(3,), hi(3,))]
+
+    def raycast(self, o, d):
+        t = _ray_room_exit(o, d, self.lo, self.hi)
+        for c, r in self.spheres:
+            t = np.minimum(t, _ray_sphere(o, d, c, r))
+        for blo, bhi in self.boxes:
+            t = np.minimum(t, _ray_box(o, d, blo, bhi))
+        return t
+
+    def free_clearance(self, x):
+        """Distance from point x to the nearest obstacle surface (positive in free space)."""
+        x = np.asarray(x, np.float64)
+        dist = min(np.min(x - self.lo), np.min(self.hi - x))
+        for c, r in self.spheres:
+            dist = min(dist, np.linalg.norm(x - c) - r)
+        for blo, bhi in self.boxes:
+            q = np.maximum(np.maximum(blo - x, x - bhi), 0.0)
+            dist = min(dist, np.linalg.norm(q) if np.any(q > 0) else -1.0)
+        return dist
+
+
+@dataclasses.dataclass
+class PlanesScene:
+    """Union of half-spaces' boundary planes seen from inside: n.x = off (n points into the wall)."""
+    normals: np.ndarray  # (k, 3) unit
+    offsets: np.ndarray  # (k,)
+
+    def raycast(self, o, d):
+        t = np.full(d.shape[0], np.inf)
+        for n, off in zip(self.normals, self.offsets):
+            dn = d @ n
+            with np.errstate(divide="ignore", invalid="ignore"):
+                tt = (off - o @ n) / dn
+            t = np.minimum(t, np.where((dn > 1e-12) & (tt > 1e-9), tt, np.inf))
+        return t
+
+    def sdf(self, x):
+        """Inside-positive distance of the 'outside the room' region: max_k (n_k.x - off_k)."""
+        vals = np.stack([x @ n - off for n, off in zip(self.normals, self.offsets)], axis=-1)
+        k = np.argmax(vals, axis=-1)
+        psi = np.take_along_axis(vals, k[..., None], axis=-1)[..., 0]
+        g = self.normals[k]
+        return psi, g
+
+
+def render_depth(scene, cam: Camera, T_wc: np.ndarray) -> np.ndarray:
+    """FP64 ray cast of `scene` from pose T_wc; returns an (H, W) FP32 z-depth image, 0 = miss."""
+    dc = cam.ray_dirs_cam()
+    d = dc @ T_wc[:3, :3].T
+    o = T_wc[:3, 3]
+    t = scene.raycast(o, d)  # ray parameter == z-depth since dc has unit z
+    depth = np.where(np.isfinite(t), t, 0.0)
+    return depth.reshape(cam.height, cam.width).astype(np.float32)
+
+
+def add_depth_noise(depth: np.ndarray, rng: np.random.Generator, k=0.0012) -> np.ndarray:
+    """Axial noise with standard deviation k z^2 (Kinect-like), zeros kept as misses."""
+    z = depth.astype(np.float64)
+    noisy = z + rng.normal(size=z.shape) * (k * z * z)
+    noisy = np.where(z > 0, np.maximum(noisy, 0.0), 0.0)
+    return noisy.astype(np.float32)
+
+
+# --------------------------------------------------------------------------------------------
+# the dense-sphere workload (64^3 grid, 2 cm voxels, sphere r = 0.4 m at the grid centre)
+# --------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class DenseSphereCase:
+    cam: Camera
+    voxel_size: float
+    truncation: float
+    dims: tuple
+    origin: tuple  # integer coordinate of voxel (0, 0, 0)
+    psi: np.ndarray  # (dz, dy, dx) FP32, x fastest
+    grad: np.ndarray  # (dz, dy, dx, 3) FP32
+    weight: np.ndarray  # (dz, dy, dx) FP32
+    depth: np.ndarray  # (H, W) FP32
+    T_gt: np.ndarray
+    T_init: np.ndarray
+    scene: SphereScene
+    n_iters: int = 20
+
+
+def dense_sphere_case(seed: int = 1, dims=64, voxel_size=0.02, radius=0.4, distance=1.2,
+                      cam: Camera = TINY_160, n_iters: int = 20) -> DenseSphereCase:
+    """Analytic sphere SDF on a dense grid plus one depth image from a seed-random viewpoint."""
+    rng = np.random.default_rng(seed)
+    T = 5 * voxel_size
+    half = dims // 2
+    origin = (-half, -half, -half)
+    m = np.arange(dims) - half
+    mz, my, mx = np.meshgrid(m, m, m, indexing="ij")
+    vox = np.stack([mx, my, mz], axis=-1).astype(np.float64) * np.float64(np.float32(voxel_size))
+    scene = SphereScene(np.zeros(3), radius)
+    psi, g = scene.sdf(vox)
+    w = (np.abs(psi) <= T).astype(np.float32)
+    g = np.nan_to_num(g)
+    direction = rng.normal(size=3)
+    direction /= np.linalg.norm(direction)
+    T_gt = look_at(distance * direction, np.zeros(3), roll=rng.uniform(-math.pi, math.pi))
+    depth = render_depth(scene, cam, T_gt)
+    T_init = perturb_pose(T_gt, rng, 5.0, 0.05)
+    return DenseSphereCase(cam, voxel_size, T, (dims, dims, dims), origin,
+                           psi.astype(np.float32), g.astype(np.float32), w, depth, T_gt, T_init,
+                           scene, n_iters)
+
+
+# --------------------------------------------------------------------------------------------
+# the hashed room workload (4x4x3 m room, 10 spheres, 6 boxes, smooth trajectory)
+# --------------------------------------------------------------------------------------------
+
+
+def make_room(seed: int, size=(4.0, 4.0, 3.0), n_spheres=10, n_boxes=6) -> RoomScene:
+    """Room with inward-facing walls and seed-placed, non-overlapping spheres and boxes."""
+    rng = np.random.default_rng(seed)
+    lo = np.zeros(3)
+    hi = np.asarray(size, np.float64)
+    placed = []  # bounding spheres (c, r) for overlap rejection
+    spheres, boxes = [], []
+    margin = 0.05
+
+    def free(c, r):
+        return all(np.linalg.norm(c - pc) > r + pr + margin for pc, pr in placed)
+
+    while len(boxes) < n_boxes:
+        half = rng.uniform(0.1, 0.4, size=3)
+        c = np.array([rng.uniform(0.3 + half[0], hi[0] - 0.3 - half[0]),
+                      rng.uniform(0.3 + half[1], hi[1] - 0.3 - half[1]),
+                      half[2]])  # resting on the floor
+        r = float(np.linalg.norm(half))
+        if free(c, r):
+            placed.append((c, r))
+            boxes.append((c - half, c + half))
+    while len(spheres) < n_spheres:
+        r = rng.uniform(0.1, 0.4)
+        c = np.array([rng.uniform(r + 0.2, hi[0] - r - 0.2), rng.uniform(r + 0.2, hi[1] - r - 0.2),
+                      rng.uniform(r + 0.1, hi[2] - r - 0.2)])
+        if free(c, r):
+            placed.append((c, r))
+            spheres.append((c, float(r)))
+    return RoomScene(lo, hi, spheres, boxes)
+
+
+def _bspline(ctrl: np.ndarray, s: np.ndarray) -> np.ndarray:
+    """Uniform cubic B-spline through control rows `ctrl`, evaluated at s in [0, len(ctrl) - 3)."""
+    i = np.clip(np.floor(s).astype(int), 0, len(ctrl) - 4)
+    u = (s - i)[:, None]
+    b0 = (1 - u) ** 3 / 6
+    b1 = (3 * u**3 - 6 * u**2 + 4) / 6
+    b2 = (-3 * u**3 + 3 * u**2 + 3 * u + 1) / 6
+    b3 = u**3 / 6
+    return b0 * ctrl[i] + b1 * ctrl[i + 1] + b2 * ctrl[i + 2] + b3 * ctrl[i + 3]
+
+
+def room_trajectory(scene: RoomScene, n_frames: int, seed: int, frames_per_segment=25,
+                    step=0.5) -> list:
+    """Smooth camera path: B-spline over a seeded random walk of positions and look-at targets.
+
+    Positions stay >= 0.35 m from every surface and >= 0.7 m from the walls; about step /
+    frames_per_segment metres of motion per frame (2 cm at the defaults)."""
+    rng = np.random.default_rng(seed + 7919)
+    n_ctrl = n_frames // frames_per_segment + 4
+    center = 0.5 * (scene.lo + scene.hi)
+    pos = [center.copy()]
+    while scene.free_clearance(pos[0]) < 0.35:
+        pos[0] = center + rng.uniform(-0.8, 0.8, size=3) * np.array([1, 1, 0.3])
+    tries = 0
+    while len(pos) < n_ctrl:
+        cand = pos[-1] + step * _unit(rng.normal(size=3) * np.array([1, 1, 0.4]))
+        ok = np.all(cand > scene.lo + 0.7) and np.all(cand < scene.hi - 0.7)
+        if ok and scene.free_clearance(cand) > 0.35:
+            pos.append(cand)
+            tries = 0
+        else:
+            tries += 1
+            if tries > 200:  # back off toward the centre
+                pos.append(0.5 * (pos[-1] + center))
+    pos = np.array(pos)
+    tgt = [center + rng.uniform(-1, 1, size=3) * np.array([1.2, 1.2, 0.6])]
+    while len(tgt) < n_ctrl:
+        tgt.append(np.clip(tgt[-1] + 0.6 * _unit(rng.normal(size=3)), scene.lo + 0.2, scene.hi - 0.2))
+    tgt = np.array(tgt)
+    s = np.arange(n_frames, dtype=np.float64) / frames_per_segment
+    P = _bspline(pos, s)
+    Q = _bspline(tgt, s)
+    poses = []
+    for p, q in zip(P, Q):
+        if np.linalg.norm(q - p) < 0.5:  # keep the target away from the camera
+            q = p + 0.5 * _unit(q - p + 1e-3)
+        poses.append(look_at(p, q))
+    return poses
+
+
+def _unit(x):
+    return x / np.linalg.norm(x)
+
+
+@dataclasses.dataclass
+class RoomSequence:
+    cam: Camera
+    scene: RoomScene
+    poses: list  # ground-truth T_wc per frame
+    depths: np.ndarray  # (F, H, W) FP32, noisy
+    voxel_size: float
+    truncation: float
+
+
+def room_sequence(seed: int = 2, n_frames: int = 100, cam: Camera = KINECT_640, voxel_size=0.01,
+                  noise=True, frames_per_segment=25) -> RoomSequence:
+    """Room scene, smooth trajectory and noisy depth frames (sigma = 0.0012 z^2)."""
+    scene = make_room(seed)
+    poses = room_trajectory(scene, n_frames, seed, frames_per_segment)
+    rng = np.random.default_rng(seed + 104729)
+    depths = np.empty((n_frames, cam.height, cam.width), np.float32)
+    for f, T in enumerate(poses):
+        d = render_depth(scene, cam, T)
+        depths[f] = add_depth_noise(d, rng) if noise else d
+    return RoomSequence(cam, scene, poses, depths, voxel_size, 5 * voxel_size)
