@@ -1,0 +1,383 @@
+"""Benchmark: Gradient-SDF tracking + fusion on the hashed room workload.
+
+Workload (one "step" = one frame of a SLAM loop): a 640x480 depth frame of a synthetic room
+(4x4x3 m, 10 spheres, 6 boxes, noise sigma = 0.0012 z^2) on a smooth 100-frame trajectory,
+8^3-block hashed map with 1 cm voxels, T = 5 cm.  Per frame: 10 Gauss-Newton tracking steps
+against the map (from the previous frame's estimate), then fusion of the frame at the tracked
+pose.  Frame 0 is fused at its true pose.  The first W frames are warm-up, the next K are timed.
+
+value = tracked depth pixels per second per Gauss-Newton iteration over the whole step
+        (H*W pixels x 10 iterations x K frames / summed step time);
+fused_voxels_per_s = ray-voxel updates per second over the same time.
+Inputs (all depth frames) are resident in HBM before timing; L2 is flushed (a 512 MB write)
+between timed steps, outside the timed interval.  e2e repeats the run through the same API
+with each frame copied from pinned host memory and the pose read back inside the interval.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsdf|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tracked depth px/s per GN iteration & fused voxels/s; % of HBM peak"
+GN_ITERS = 10
+SEED = 2
+VOXEL = 0.01
+HASH_SLOTS = 1 << 18
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes per unit: tracking reads 4 B of depth per pixel and, for each
+# pixel with a usable voxel, one 8 B key probe and the 20 B payload; fusion reads 4 B of depth per
+# pixel and each ray-voxel update probes an 8 B key and read-modify-writes the 20 B payload.
+TRACK_B_PER_PX = 4
+TRACK_B_PER_VALID = 8 + 20
+INT_B_PER_PX = 4
+INT_B_PER_VISIT = 8 + 2 * 20
+
+
+def workload_name(n_frames):
+    return (f"hashed room, 640x480 depth, 8^3 blocks, 1 cm voxels, T=5 cm, {n_frames}-frame spline "
+            f"trajectory, {GN_ITERS} GN iterations + 1 fusion per frame")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2111_13652_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sms, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def make_sequence(n_frames):
+    from paper_2111_13652_gb300 import inputs as I
+
+    return I.room_sequence(seed=SEED, n_frames=n_frames, voxel_size=VOXEL)
+
+
+# -----------------------------------------------------------------------------------------------
+# oracle (CPU) timing: the reference arm and the cpu_baseline leg
+# -----------------------------------------------------------------------------------------------
+
+
+def run_oracle(seq, first, count):
+    """Oracle SLAM loop: fuse frame 0 at its true pose, then frames 1..first+count-1 with
+    tracking; returns the time of frames first..first+count-1 and their units."""
+    from oracle import oracle as O
+
+    om = O.OracleMap(O.params(VOXEL))
+    om.integrate(seq.depths[0], seq.cam, seq.poses[0])
+    T = seq.poses[0].copy()
+    t_sum, visits = 0.0, 0
+    for f in range(1, first + count):
+        t0 = time.perf_counter()
+        for _ in range(GN_ITERS):
+            T, _ = om.track_step(seq.depths[f], seq.cam, T)
+        st = om.integrate(seq.depths[f], seq.cam, T)
+        dt = time.perf_counter() - t0
+        if f >= first:
+            t_sum += dt
+            visits += st.n_visits
+    px = seq.cam.width * seq.cam.height * GN_ITERS * count
+    return t_sum, px, visits
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = max(100, 1 + args.warmup + args.steps)
+    seq = make_sequence(1 + args.warmup + args.steps)  # the trajectory's prefix is independent of its length
+    first = 1 + args.warmup
+    t, px, visits = run_oracle(seq, first, args.steps)
+    value = px / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(n)},
+            "fused_voxels_per_s": visits / t,
+            "cpu_baseline": {"value": value, "unit": "px/s", "cores": 1, "kind": "oracle",
+                             "sample": f"frames {first}..{first + args.steps - 1} of the workload, single-threaded"},
+            "e2e": {"value": value, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -----------------------------------------------------------------------------------------------
+# GPU arm
+# -----------------------------------------------------------------------------------------------
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_2111_13652_gb300 import gsdf as G
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    G.load_library()
+    n_frames = max(100, 1 + args.warmup + args.steps)
+    seq = make_sequence(n_frames)
+    H, W = seq.cam.height, seq.cam.width
+    K = G.intrinsics(seq.cam)
+    stream = torch.cuda.current_stream(dev)
+    depths = torch.from_numpy(seq.depths).to(dev)  # inputs resident in HBM
+    gt0 = torch.from_numpy(np.ascontiguousarray(seq.poses[0])).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    n_steps_total = args.warmup + args.steps
+    first = 1
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def run(e2e: bool):
+        m = G.Map(G.make_config(VOXEL, hash_slots=HASH_SLOTS), stream)
+        pose = gt0.clone()
+        dbuf = torch.empty((H, W), dtype=torch.float32, device=dev)  # depth staging buffer
+        dbuf.copy_(depths[0])
+        m.integrate(dbuf, K, pose)
+        # the graph-replayed calls write fixed statistics buffers; they are copied out per step
+        tbuf = m.new_track_stats(GN_ITERS)
+        ibuf = m.new_integrate_stats()
+        tstats = torch.zeros((args.steps, GN_ITERS, G.TRACK_STATS_BYTES), dtype=torch.uint8, device=dev)
+        istats = torch.zeros((args.steps, G.INTEGRATE_STATS_BYTES), dtype=torch.uint8, device=dev)
+        host_depth = torch.from_numpy(seq.depths).pin_memory() if e2e else None
+        host_pose = torch.empty(16, dtype=torch.float64).pin_memory()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        launches = 0
+        for s in range(n_steps_total):
+            f = first + s
+            timed = s >= args.warmup
+            k = s - args.warmup
+            if timed and k == 0:
+                barrier()
+                wall0 = time.perf_counter()
+            if timed:
+                flush.fill_(s & 0xFF)  # evict L2 before the step (not timed)
+                ev[k][0].record(stream)
+            dbuf.copy_(host_depth[f] if e2e else depths[f], non_blocking=True)
+            if timed:
+                ev[k][1].record(stream)
+            m.track(dbuf, K, pose, GN_ITERS, tbuf)
+            if timed:
+                ev[k][2].record(stream)
+            m.integrate(dbuf, K, pose, ibuf)
+            if e2e:
+                host_pose.copy_(pose.view(-1), non_blocking=True)
+            if timed:
+                ev[k][3].record(stream)
+                launches += GN_ITERS + 2  # tracking steps, fusion kernel, statistics kernel
+                tstats[k].copy_(tbuf)
+                istats[k].copy_(ibuf)
+            if e2e:
+                stream.synchronize()
+        barrier()
+        wall = time.perf_counter() - wall0
+        m.sync()
+        step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
+        track_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
+        int_ms = np.array([e[2].elapsed_time(e[3]) for e in ev])
+        ts = tstats.cpu().numpy()
+        ist = istats.cpu().numpy()
+        n_valid = np.array([[G.track_stats_from_bytes(ts[k, i]).n_valid for i in range(GN_ITERS)]
+                            for k in range(args.steps)])
+        visits = np.array([G.integrate_stats_from_bytes(ist[k]).n_visits for k in range(args.steps)])
+        blocks = G.integrate_stats_from_bytes(ist[-1]).n_blocks_total
+        final_pose = pose.cpu().numpy()
+        m.close()
+        return dict(step_ms=step_ms, track_ms=track_ms, int_ms=int_ms, n_valid=n_valid, visits=visits,
+                    blocks=blocks, wall=wall, launches=launches, pose=final_pose)
+
+    with ClockSampler(local) as clk:
+        r = run(e2e=False)
+        r2 = run(e2e=True)
+    clocks = clk.summary()
+    clocks["window"] = "whole GPU run (warm-up, timed steps, e2e repeat); 100 ms sampling"
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    t_total = reduce_max(float(r["step_ms"].sum()) / 1e3)
+    t_e2e = reduce_max(float(r2["step_ms"].sum()) / 1e3)
+    px_units = H * W * GN_ITERS * args.steps
+    value = world * px_units / t_total
+    visits_total = float(r["visits"].sum())
+    # roofline of the two kernels; the dominant one (larger share of step time) is reported
+    hbm, hbm_kind = measured_hbm_peak()
+    track_bytes = TRACK_B_PER_PX * H * W + TRACK_B_PER_VALID * r["n_valid"]  # per launch
+    track_gbs = float(track_bytes.sum() / (r["track_ms"].sum() / 1e3) / 1e9)  # 10 launches per interval
+    int_bytes = INT_B_PER_PX * H * W + INT_B_PER_VISIT * r["visits"]
+    int_gbs = float(int_bytes.sum() / (r["int_ms"].sum() / 1e3) / 1e9)
+    share_track = float(r["track_ms"].sum() / r["step_ms"].sum())  # the rest: staging copy
+    share_int = float(r["int_ms"].sum() / r["step_ms"].sum())
+    if share_int >= share_track:
+        dom, ach, traffic = "integrate_kernel", int_gbs, profiled_traffic("integrate_kernel")
+    else:
+        dom, ach, traffic = "track_kernel", track_gbs, profiled_traffic("track_kernel")
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "kernel": dom, "peak_source": hbm_kind,
+            "kernels": {"track_kernel": {"GBs": track_gbs, "share": share_track,
+                                         "us_per_launch": 1e3 * float(r["track_ms"].mean()) / GN_ITERS},
+                        "integrate_kernel": {"GBs": int_gbs, "share": share_int,
+                                             "us_per_launch": 1e3 * float(r["int_ms"].mean())}}}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        first_cpu, count = 1, 3
+        t_cpu, px_cpu, _ = run_oracle(seq, first_cpu, count)
+        cpu = {"value": px_cpu / t_cpu, "unit": "px/s", "cores": 1, "kind": "oracle",
+               "sample": f"frames {first_cpu}..{first_cpu + count - 1} of the same sequence "
+                         f"({GN_ITERS} GN steps + fusion each), single-threaded"}
+    if rank == 0:
+        gt = seq.poses[first + n_steps_total - 1]
+        line = {
+            "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(n_frames), "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"{world} independent replica(s)", "hash_slots": HASH_SLOTS},
+            "fused_voxels_per_s": world * visits_total / t_total,
+            "track_px_per_s_kernel_only": H * W * GN_ITERS * args.steps / (r["track_ms"].sum() / 1e3),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * px_units / t_e2e, "unit": "px/s", "h2d_bytes_per_step": H * W * 4,
+                    "d2h_bytes_per_step": 16 * 8},
+            "gpu_launches": r["launches"],
+            "clocks": clocks,
+            "blocks_allocated": int(r["blocks"]),
+            "final_pose_error_m": float(np.linalg.norm(r["pose"][:3, 3] - gt[:3, 3])),
+            "wall_s_timed_region": r["wall"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=95)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="gsdf", choices=["gsdf", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

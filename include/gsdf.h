@@ -1,0 +1,209 @@
+/*
+ * gsdf.h -- C ABI of the GB300 Gradient-SDF tracking and fusion library (libgsdf.so).
+ *
+ * The library implements the data-parallel hot path of "Gradient-SDF: A Semi-Implicit Surface
+ * Representation for 3D Reconstruction" (Sommer et al., CVPR 2022):
+ *   - a voxel map storing per voxel a signed distance psi, a gradient g and a weight W
+ *     (Sec. 3.2, the GradSdfVoxel of Sec. 5.1), either a dense box of voxels or a hash table of
+ *     8^3 voxel blocks (Sec. 3.1);
+ *   - depth-image fusion, Eqs. (sdf_update) and (gradient_update), pixel-driven as in Sec. 5.3;
+ *   - direct SDF camera tracking, Eq. (tracking), with the one-lookup first-order model
+ *     Eq. (taylor), solved by Gauss-Newton with a Cholesky factorisation (Sec. 5.1).
+ * Every step runs in the library's own CUDA kernels (sm_103a); there is no CPU fallback.
+ *
+ * Conventions
+ *   - Depth images: FP32, row-major H x W, z-depth in metres, 0 (or anything outside
+ *     (0, depth_max]) = no measurement.  Pixel (u, v) has integer coordinates.
+ *   - Poses T_wc: 16 FP64 values, row-major 4x4, camera -> world (P = R p + t).
+ *   - Voxel centres v = voxel_size * m, m in Z^3 (Sec. 3.1).  Block of m: floor(m / 8);
+ *     local index (m mod 8): x + 8 y + 64 z.
+ *   - Signed distances are inside-positive (negative in free space, Sec. 3.1); g points into
+ *     the surface.
+ *   - "_dev" pointers are CUDA device pointers; all other pointers are host pointers.
+ *
+ * Streams and ordering: every call is issued on the handle's stream (gsdf_create /
+ * gsdf_set_stream) and returns without waiting, except gsdf_create, gsdf_destroy,
+ * gsdf_upload_dense, gsdf_load_voxels, gsdf_extract_voxels, gsdf_num_blocks and gsdf_sync,
+ * which synchronise the stream.  Caller-owned device buffers must stay valid until the stream
+ * work that uses them has completed.  A handle must not be used from two threads at once.
+ * gsdf_integrate, gsdf_track_step and gsdf_track allocate no device memory.
+ *
+ * Errors: argument errors are returned at once and leave the state unchanged.  Errors found on
+ * the device (hash capacity exhausted) are recorded in a sticky device word, returned by the
+ * next gsdf_sync (which clears it).  A degenerate tracking system is not an error of the map:
+ * it is reported in gsdf_track_stats.status and leaves the pose unchanged.  Nothing aborts,
+ * traps or prints.
+ */
+#ifndef GSDF_H
+#define GSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSDF_OK = 0,
+    GSDF_ERR_INVALID_ARG = 1,  /* a null pointer, a bad size or an inconsistent configuration */
+    GSDF_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    GSDF_ERR_OOM = 3,          /* device allocation failed in gsdf_create / extraction */
+    GSDF_ERR_CAPACITY = 4,     /* the hash table ran out of slots (probe limit reached) */
+    GSDF_ERR_DEGENERATE = 5,   /* singular tracking system (see gsdf_track_stats.status) */
+    GSDF_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    GSDF_ERR_NO_VALID_PIXELS = 7
+} gsdf_status;
+
+enum { GSDF_GRID_DENSE = 0, GSDF_GRID_HASHED = 1 };
+
+/* Pinhole intrinsics (Sec. 5.3 uses 640x480 TUM frames, depth cut off at 3.5 m). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float depth_max;
+} gsdf_intrinsics;
+
+/* Map and method configuration.
+ *   grid_kind      GSDF_GRID_DENSE or GSDF_GRID_HASHED
+ *   dense_dims     dense grid size in voxels (x, y, z); dense only
+ *   dense_origin   integer coordinate m of dense voxel (0, 0, 0); dense only
+ *   voxel_size     v_s in metres (Sec. 3.1)
+ *   truncation     T in metres (Sec. 5.3 uses 5 v_s); must be >= voxel_size / 2
+ *   weight_eps     knee of the linear fusion weight: w = 1 for d <= eps, falling linearly to 0
+ *                  at d = T (Sec. 5.3, "linear weight"); 0 <= eps < T
+ *   huber_delta    threshold of the Huber tracking weight w_k of Eq. (tracking)
+ *   cos_max_angle  cosine of the largest normal/viewing-ray angle integrated (Sec. 5.3: 75 deg)
+ *   damping        relative Levenberg-Marquardt damping: H + damping * mean(diag H) * I;
+ *                  0 = plain Gauss-Newton (Sec. 5.1)
+ *   hash_slots     number of hash slots (power of two); each slot owns one 8^3 block payload
+ *                  (10 KB); hashed only
+ *   max_probe      linear-probe limit of the hash table (> 0); hashed only */
+typedef struct {
+    int32_t grid_kind;
+    int32_t dense_dims[3];
+    int32_t dense_origin[3];
+    float voxel_size;
+    float truncation;
+    float weight_eps;
+    float huber_delta;
+    float cos_max_angle;
+    double damping;
+    int64_t hash_slots;
+    int32_t max_probe;
+    int32_t reserved;
+} gsdf_config;
+
+/* Written by gsdf_track_step into device memory.  H is the upper triangle (row-major, 21
+ * values) of sum_k w_k J_k J_k^T and b = sum_k w_k J_k r_k, both at the *input* pose;
+ * J = (P x ghat, ghat) for the left increment T <- exp(xi^) T, xi = (omega, upsilon). */
+typedef struct {
+    double H[21];
+    double b[6];
+    double energy;    /* sum_k w_k r_k^2 */
+    int64_t n_valid;  /* pixels with a usable voxel */
+    int64_t n_huber;  /* of those, |r| > huber_delta */
+    int32_t status;   /* GSDF_OK, or GSDF_ERR_DEGENERATE (pose left unchanged) */
+    int32_t pad;
+    double xi[6];     /* the increment applied (zero if degenerate) */
+} gsdf_track_stats;
+
+/* Written by gsdf_integrate into device memory (counts of this call, except n_blocks_total). */
+typedef struct {
+    int64_t n_rays;          /* pixels that passed the depth and normal tests */
+    int64_t n_visits;        /* ray-voxel updates with weight > 0 */
+    int64_t n_blocks_new;    /* hash blocks allocated by this call */
+    int64_t n_blocks_total;  /* hash blocks allocated so far */
+} gsdf_integrate_stats;
+
+/* One voxel with W > 0, as returned by gsdf_extract_voxels (32 bytes).  psi is the fused
+ * signed distance, g the unnormalised weighted sum of normals (ghat = g / |g|), w = W. */
+typedef struct {
+    int32_t m[3];
+    float psi;
+    float g[3];
+    float w;
+} gsdf_voxel;
+
+typedef struct gsdf_handle gsdf_handle;
+
+/* Create a map on the current CUDA device.  Allocates the table, the voxel payload (zeroed:
+ * psi = 0, g = 0, W = 0) and all scratch used by integrate/track; nothing is allocated later
+ * on those paths.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Returns GSDF_ERR_INVALID_ARG on a bad configuration, GSDF_ERR_OOM if allocation fails. */
+gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle** out);
+
+/* Free every device and host resource of the handle (synchronises its stream first). */
+gsdf_status gsdf_destroy(gsdf_handle* h);
+
+/* Change the stream subsequent calls are issued on. */
+gsdf_status gsdf_set_stream(gsdf_handle* h, void* cuda_stream);
+
+/* Dense grids only: overwrite every voxel from host arrays (x fastest, then y, then z):
+ * psi[n], g[3n] (xyz interleaved), w[n], n = dims[0] * dims[1] * dims[2].  Voxels with w = 0
+ * count as unobserved.  Synchronous. */
+gsdf_status gsdf_upload_dense(gsdf_handle* h, const float* psi, const float* g, const float* w);
+
+/* Fuse one depth frame at pose T_wc_dev (Eqs. sdf_update, gradient_update; Sec. 5.3).
+ * For every pixel whose depth is valid and whose normal (cross product of central differences
+ * of its back-projected 4-neighbours, oriented away from the camera) makes an angle with the
+ * viewing ray below acos(cos_max_angle), the samples z_k = D + (k - K) v_s / 2, k = 0..2K,
+ * K = ceil(T / (v_s / 2)), are rounded to voxels; each distinct voxel of the ray with
+ * d = z_v - D in [-T, T) (z_v: camera depth of the voxel centre) receives
+ * (w d, w, w R n) with the linear weight w.  Hashed grids allocate the block of every voxel
+ * that receives an update; dense grids skip voxels outside the box.  The result equals the
+ * sequential running average of Eq. (sdf_update) up to floating-point summation order.
+ * depth_dev: H*W FP32 on the device.  T_wc_dev: 16 FP64 on the device.
+ * stats_dev: optional (NULL allowed) device gsdf_integrate_stats, overwritten. */
+gsdf_status gsdf_integrate(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
+                           const double* T_wc_dev, gsdf_integrate_stats* stats_dev);
+
+/* One Gauss-Newton step of Eq. (tracking) with the model of Eq. (taylor) (Sec. 4.1, 5.1).
+ * For every valid pixel, P = R p + t, the nearest voxel m = floor(P / v_s + 1/2) is looked up;
+ * if it exists with W > 0 and g != 0, r = psi + ghat.(P - v_s m), J = (P x ghat, ghat),
+ * w = Huber(r).  The normal equations are reduced on the device, (H + lambda I) xi = -b is
+ * solved by Cholesky in FP64 and T_wc_dev is replaced by exp(xi^) T_wc_dev, all without
+ * a host round trip.  If fewer than 6 pixels are usable or a pivot is <= 1e-12 max diag(H),
+ * the pose is left unchanged and stats.status = GSDF_ERR_DEGENERATE.
+ * T_wc_dev: 16 FP64 on the device, read and written.  stats_dev: optional (NULL allowed). */
+gsdf_status gsdf_track_step(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
+                            double* T_wc_dev, gsdf_track_stats* stats_dev);
+
+/* n_iters consecutive Gauss-Newton steps, each exactly gsdf_track_step, in one call.
+ * stats_dev: NULL or a device array of n_iters gsdf_track_stats (entry k describes step k).
+ * Unless the handle's stream is being captured by the caller (then the kernels are simply
+ * launched into the caller's capture), the n_iters launches are recorded once into a CUDA graph
+ * that is replayed while (depth_dev, *K, T_wc_dev, stats_dev, n_iters) stay the same; a call
+ * with other arguments records a new graph (host-side cost, no device allocation by the
+ * library).  Reusing one depth staging buffer and one stats buffer keeps every call a replay.
+ * 1 <= n_iters <= 1024. */
+gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
+                       double* T_wc_dev, int32_t n_iters, gsdf_track_stats* stats_dev);
+
+/* Copy every voxel with W > 0 to host_out, ordered by block (lexicographic block coordinate)
+ * and then local index for hashed grids, by linear index (x fastest) for dense grids.
+ * *count_out receives the number of such voxels even if it exceeds capacity (then only the
+ * first `capacity` are written and GSDF_ERR_CAPACITY is returned).  Synchronous; may allocate
+ * temporary device memory. */
+gsdf_status gsdf_extract_voxels(gsdf_handle* h, gsdf_voxel* host_out, size_t capacity,
+                                size_t* count_out);
+
+/* Checkpoint restore: write n voxels (unique m; w > 0) into the map, allocating blocks as
+ * needed.  Voxels of a dense map outside its box are rejected with GSDF_ERR_INVALID_ARG.
+ * Round trip extract -> load -> extract reproduces m, g and w exactly and psi to within one
+ * FP32 rounding.  Synchronous; may allocate temporary device memory. */
+gsdf_status gsdf_load_voxels(gsdf_handle* h, const gsdf_voxel* host_in, size_t n);
+
+/* Number of allocated hash blocks (dense: number of 512-voxel chunks).  Synchronous. */
+gsdf_status gsdf_num_blocks(gsdf_handle* h, int64_t* n_out);
+
+/* Wait for the handle's stream; return (and clear) the first device-detected error. */
+gsdf_status gsdf_sync(gsdf_handle* h);
+
+/* Static description of a status code. */
+const char* gsdf_status_string(gsdf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSDF_H */

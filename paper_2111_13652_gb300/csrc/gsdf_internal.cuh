@@ -1,0 +1,239 @@
+// Internal device-side definitions shared by the library's kernels (not part of the C ABI).
+//
+// Map layout in HBM
+//   dense:  payload arrays indexed by the linear voxel index (x fastest) of the box;
+//   hashed: an open-addressing table of 2^k slots of packed 64-bit block keys; slot s owns the
+//           payload of one 8^3 block, voxels s * 512 + local (local = x + 8 y + 64 z).
+//   payload per voxel: float4 A = (W psi, g.x, g.y, g.z) and float W -- 20 bytes, in two
+//   arrays so that one 16-byte vector load/atomic covers A.  Storing W psi (not psi) makes the
+//   running average of Eq. (sdf_update) a pure sum, order-independent and atomic-friendly:
+//   psi = A.x / W when read.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsdf.h"
+
+namespace gsdf {
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kBlockVoxels = 512;
+constexpr int kBias = 1 << 20;  // block coordinates are stored biased by 2^20 in 21 bits
+
+// Device-side error word codes (first error wins).
+constexpr int kErrNone = 0;
+
+struct Intr {
+    float fx, fy, cx, cy;
+    int width, height;
+    float depth_max;
+    float ifx, ify;  // (float)(1 / fx) computed in FP64 then rounded once
+};
+
+struct Params {
+    float vs, inv_vs, trunc, eps, half_vs, huber, cos_max;
+    int band_half;  // K = ceil(T / (v_s / 2))
+    double damping;
+};
+
+// Pose rounded once from FP64: camera->world (R, t) and world->camera (R^T, -R^T t).
+struct PoseF {
+    float R[9], t[3], RT[9], tinv[3];
+};
+
+// ------------------------------------------------------------------------------------------
+// block keys and hashing
+// ------------------------------------------------------------------------------------------
+
+__host__ __device__ inline int floor_div8(int m) { return m >> 3; }  // arithmetic shift = floor
+
+__host__ __device__ inline unsigned long long pack_block(int bx, int by, int bz) {
+    return ((unsigned long long)(unsigned)(bx + kBias) << 42) |
+           ((unsigned long long)(unsigned)(by + kBias) << 21) |
+           (unsigned long long)(unsigned)(bz + kBias);
+}
+
+__host__ __device__ inline void unpack_block(unsigned long long k, int* b) {
+    b[0] = (int)((k >> 42) & 0x1FFFFF) - kBias;
+    b[1] = (int)((k >> 21) & 0x1FFFFF) - kBias;
+    b[2] = (int)(k & 0x1FFFFF) - kBias;
+}
+
+__host__ __device__ inline bool block_in_range(int bx, int by, int bz) {
+    return bx >= -kBias && bx < kBias && by >= -kBias && by < kBias && bz >= -kBias && bz < kBias;
+}
+
+__host__ __device__ inline unsigned long long mix64(unsigned long long k) {
+    k ^= k >> 31;
+    k *= 0x7FB5D329728EA185ull;
+    k ^= k >> 27;
+    k *= 0x81DADEF4BC2DD44Dull;
+    k ^= k >> 33;
+    return k;
+}
+
+// ------------------------------------------------------------------------------------------
+// maps
+// ------------------------------------------------------------------------------------------
+
+struct DenseMap {
+    float4* A;
+    float* W;
+    int dims[3];
+    int origin[3];
+
+    __device__ __forceinline__ long long find(int mx, int my, int mz) const {
+        int x = mx - origin[0], y = my - origin[1], z = mz - origin[2];
+        if ((unsigned)x >= (unsigned)dims[0] || (unsigned)y >= (unsigned)dims[1] ||
+            (unsigned)z >= (unsigned)dims[2])
+            return -1;
+        return ((long long)z * dims[1] + y) * dims[0] + x;
+    }
+    // Dense voxels always exist inside the box.
+    __device__ __forceinline__ long long find_or_insert(int mx, int my, int mz, int* /*err*/,
+                                                        unsigned int* /*n_new*/) const {
+        return find(mx, my, mz);
+    }
+};
+
+struct HashMap {
+    unsigned long long* keys;
+    float4* A;
+    float* W;
+    unsigned long long mask;  // slots - 1
+    int max_probe;
+
+    __device__ __forceinline__ long long find(int mx, int my, int mz) const {
+        int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
+        if (!block_in_range(bx, by, bz)) return -1;
+        unsigned long long key = pack_block(bx, by, bz);
+        unsigned long long s = mix64(key) & mask;
+        for (int p = 0; p < max_probe; ++p) {
+            unsigned long long k = __ldg(keys + s);
+            if (k == key) {
+                int local = (mx & 7) + 8 * (my & 7) + 64 * (mz & 7);
+                return (long long)s * kBlockVoxels + local;
+            }
+            if (k == kEmptyKey) return -1;
+            s = (s + 1) & mask;
+        }
+        return -1;
+    }
+
+    // Lookup-or-insert used while other threads insert concurrently.  Keys are never removed,
+    // so a stale read can only show an empty slot, which the compare-and-swap then resolves.
+    __device__ __forceinline__ long long find_or_insert(int mx, int my, int mz, int* err,
+                                                        unsigned int* n_new) const {
+        int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
+        if (!block_in_range(bx, by, bz)) {
+            atomicCAS(err, kErrNone, (int)GSDF_ERR_CAPACITY);
+            return -1;
+        }
+        unsigned long long key = pack_block(bx, by, bz);
+        unsigned long long s = mix64(key) & mask;
+        for (int p = 0; p < max_probe; ++p) {
+            unsigned long long k = __ldcg(keys + s);
+            if (k == kEmptyKey) {
+                unsigned long long prev = atomicCAS(keys + s, kEmptyKey, key);
+                if (prev == kEmptyKey) {
+                    atomicAdd(n_new, 1u);
+                    k = key;
+                } else {
+                    k = prev;
+                }
+            }
+            if (k == key) {
+                int local = (mx & 7) + 8 * (my & 7) + 64 * (mz & 7);
+                return (long long)s * kBlockVoxels + local;
+            }
+            s = (s + 1) & mask;
+        }
+        atomicCAS(err, kErrNone, (int)GSDF_ERR_CAPACITY);
+        return -1;
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// FP32 index path: correctly rounded operations in a fixed order, no contraction, so that every
+// discrete decision (validity, voxel rounding, normal test, band test) is reproducible.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ bool depth_ok(float D, float dmax) { return D > 0.0f && D <= dmax; }
+
+__device__ __forceinline__ void backproject(const Intr& K, int u, int v, float z, float p[3]) {
+    float xn = __fmul_rn(__fsub_rn((float)u, K.cx), K.ifx);
+    float yn = __fmul_rn(__fsub_rn((float)v, K.cy), K.ify);
+    p[0] = __fmul_rn(z, xn);
+    p[1] = __fmul_rn(z, yn);
+    p[2] = z;
+}
+
+__device__ __forceinline__ float dot_row(const float* r, const float p[3]) {
+    float s = __fadd_rn(__fmul_rn(r[0], p[0]), __fmul_rn(r[1], p[1]));
+    return __fadd_rn(s, __fmul_rn(r[2], p[2]));
+}
+
+__device__ __forceinline__ void xform(const float* R, const float* t, const float p[3], float P[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P[i] = __fadd_rn(dot_row(R + 3 * i, p), t[i]);
+}
+
+__device__ __forceinline__ int round_voxel(float x, float inv_vs) {
+    return (int)floorf(__fadd_rn(__fmul_rn(x, inv_vs), 0.5f));
+}
+
+__device__ __forceinline__ float dot3_rn(const float a[3], const float b[3]) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a[0], b[0]), __fmul_rn(a[1], b[1])), __fmul_rn(a[2], b[2]));
+}
+
+// Round an FP64 camera->world pose once to FP32 (R, t) and (R^T, -R^T t); -R^T t is formed in
+// FP64 as ((R_0i t_0 + R_1i t_1) + R_2i t_2) without fused multiply-adds, then rounded.
+__device__ inline void round_pose(const double* T, PoseF& q) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            q.R[3 * i + j] = __double2float_rn(T[4 * i + j]);
+            q.RT[3 * i + j] = __double2float_rn(T[4 * j + i]);
+        }
+        q.t[i] = __double2float_rn(T[4 * i + 3]);
+        double s = __dmul_rn(T[0 * 4 + i], T[3]);
+        s = __dadd_rn(s, __dmul_rn(T[1 * 4 + i], T[7]));
+        s = __dadd_rn(s, __dmul_rn(T[2 * 4 + i], T[11]));
+        q.tinv[i] = __double2float_rn(-s);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers (defined in the kernel translation units)
+// ------------------------------------------------------------------------------------------
+
+struct Scratch {
+    unsigned long long* accum;  // [kAccumWords] fixed-point grid accumulators of the tracking terms
+    unsigned int* counter;      // last-block-done ticket
+    int* err;                   // sticky device error word
+    unsigned int* n_blocks;     // number of allocated hash blocks
+    int max_track_blocks;
+};
+
+constexpr int kAccumCopies = 16;  // grid accumulators are replicated to spread atomic traffic
+constexpr int kAccumWords = kAccumCopies * 32 * 4;  // copies x 30 terms (21 H, 6 b, E, n_valid, n_huber, padded to 32) x 4 chunks
+
+cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
+                         const Params& prm, double* T_wc, gsdf_track_stats* stats,
+                         const Scratch& sc, int num_sms, cudaStream_t st);
+
+cudaError_t launch_integrate(const DenseMap* dm, const HashMap* hm, const float* depth,
+                             const Intr& K, const Params& prm, const double* T_wc,
+                             gsdf_integrate_stats* stats, const Scratch& sc, cudaStream_t st);
+
+}  // namespace gsdf
+
+namespace gsdf {
+// extraction / checkpoint (extract.cu).  *out_dev is allocated with cudaMalloc; caller frees.
+cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_slots, cudaStream_t st,
+                           int num_sms, gsdf_voxel** out_dev, long long* n_out);
+cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const gsdf_voxel* in_dev, long long n,
+                        int* err, unsigned int* n_blocks, cudaStream_t st, int num_sms);
+}  // namespace gsdf

@@ -1,0 +1,399 @@
+// Tracking: one Gauss-Newton step of Eq. (tracking) with the first-order model Eq. (taylor)
+// (Sec. 4.1), reduced and solved on the device (Sec. 5.1: Gauss-Newton + Cholesky).
+//
+// One kernel per step.  Each thread walks pixels with a grid stride, evaluates the one-lookup
+// Taylor residual and its Jacobian and accumulates the 30 unique terms (21 of H, 6 of b, E,
+// n_valid, n_huber) in FP32 registers; a warp reduce-scatters them by butterfly exchange, a
+// block combines its warps in FP64 with a fixed tree, and each block adds its row to exact
+// fixed-point grid accumulators.  The last block to finish (ticket counter, no waiting) reads
+// the sums -- identical whatever the order blocks finished in -- solves the 6x6 system in FP64,
+// applies exp(xi^) to the device pose and writes the statistics.  No host round trip per step.
+#include "gsdf_internal.cuh"
+
+namespace gsdf {
+
+constexpr int kTrackThreads = 512;
+constexpr int kTrackBlocksPerSM = 2;
+constexpr int kTrackWarps = kTrackThreads / 32;
+constexpr int kTerms = 30;
+static_assert(kAccumCopies == kTrackWarps, "the last block reads one accumulator copy per warp");
+
+// FP64 on this GPU: every FP64 warp instruction occupies the FP64 pipe for about 64 cycles,
+// whatever the number of active lanes, so FP64 code is costed in warp instructions on the
+// critical path.  The reduction and the solve keep the method's FP64 precision but use few of
+// them:
+//   * the grid-wide sum is exact fixed-point integer arithmetic (associative, hence deterministic
+//     in any order, and off the FP64 pipe);
+//   * the 6x6 system is solved by one warp holding one entry of the augmented upper triangle
+//     [H | -b] per lane (27 lanes), so that an elimination step is three FP64 instructions.
+
+// 2^k as a double (k within the normal exponent range)
+__device__ __forceinline__ double exp2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
+// e such that x * 2^-e lies in [0.5, 1), for finite x > 0 with a normal exponent
+__device__ __forceinline__ int exponent_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1022; }
+
+// Solve (H + lambda I) xi = -b, lambda = damping * mean(diag H), with one warp.  Hb (shared):
+// the 21 upper-triangle terms of H (row-major) then the 6 of b.  Degenerate (returns false,
+// xi = 0; uniform across the warp) if fewer than 6 residuals, a non-positive diagonal entry, or
+// an LDL^T pivot d_j <= 1e-12 max diag (the test of the Cholesky factorisation).
+//
+// Method: the rows and columns are scaled by powers of two s_i ~ diag_i^-1/2 (exact), then
+// eliminated without division: step j replaces every row i > j by
+//     n_j (p_j row_i - a_ij row_j),   p_j = current pivot, n_j = 2^-e with p_j n_j in [1/2, 1),
+// which equals the Schur-complement row times p_j n_j.  Row j is therefore row j of the LDL^T
+// factor scaled by sigma_j = prod_{k<j} p_k n_k, so d_j (of the scaled matrix) = p_j / sigma_j
+// and the pivot test is p_j > thr_j sigma_j with thr_j = 1e-12 maxd s_j^2, evaluated after the
+// elimination.  Back-substitution uses the six pivot reciprocals, formed in parallel.
+__device__ bool solve6_warp(const double* Hb, double damping, long long n_valid, double* xi) {
+    const int lane = threadIdx.x & 31;
+    // lane -> entry (i, k) of the augmented upper triangle, 0 <= i <= 5, i <= k <= 6 (k = 6: rhs)
+    int ei = 0, ek = 0;
+    {
+        int base = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const int len = 7 - r;
+            if (lane >= base && lane < base + len) {
+                ei = r;
+                ek = r + (lane - base);
+            }
+            base += len;
+        }
+    }
+    const bool active = lane < 27;
+    const int lane_of_ii = [&] { int b = 0; for (int r = 0; r < 6; ++r) { if (r == ei) break; b += 7 - r; } return b; }();
+    auto idx = [](int i, int k) { return i * 7 - i * (i - 1) / 2 + (k - i); };  // lane of entry (i, k), i <= k
+    auto h21 = [](int i, int k) { return i * 6 - i * (i - 1) / 2 + (k - i); };  // index in the 21 terms
+    (void)lane_of_ii;
+
+    double diag[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) diag[k] = Hb[h21(k, k)];
+    double lam = 0.0;
+    if (damping > 0.0) lam = damping * (((diag[0] + diag[1]) + (diag[2] + diag[3])) + (diag[4] + diag[5])) * (1.0 / 6.0);
+    const double maxd = fmax(fmax(fmax(diag[0], diag[1]), fmax(diag[2], diag[3])), fmax(diag[4], diag[5])) + lam;
+    bool pos = n_valid >= 6 && maxd > 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pos = pos && (diag[k] + lam) > 0.0;
+    if (lane < 6) xi[lane] = 0.0;
+    if (!pos) return false;
+    // power-of-two scales s_i (row) and s_k (column; 1 for the rhs column)
+    const double dii = Hb[h21(ei, ei)] + lam;
+    const int ekc = ek < 6 ? ek : ei;
+    const double dkk = Hb[h21(ekc, ekc)] + lam;
+    const double s_i = exp2i(-(exponent_of(dii) >> 1));
+    const double s_k = ek < 6 ? exp2i(-(exponent_of(dkk) >> 1)) : 1.0;
+    double a = 0.0;
+    if (active) a = ek < 6 ? (Hb[h21(ei, ek)] + (ei == ek ? lam : 0.0)) : -Hb[21 + ei];
+    a *= s_i * s_k;
+
+    double pn_mine = 1.0;  // lane (j, j) keeps p_j n_j of its step
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const int jj = idx(j, j);
+        // row-j lanes publish their entry normalised by n_j; the pivot's exponent sets n_j
+        const double p = __shfl_sync(0xffffffffu, a, jj);
+        const double nrm = exp2i(-exponent_of(p > 0.0 ? p : 1.0));
+        const double an = a * nrm;                                   // FP64 #1 (row j uses it)
+        const double pn = __shfl_sync(0xffffffffu, an, jj);
+        if (lane == jj) pn_mine = pn;
+        // entry (i, k), i > j: needs a_ji n_j (lane (j, i)) and a_jk (lane (j, k))
+        const int src_n = idx(j, ei > j ? ei : j);
+        const int src_k = idx(j, ek > j ? ek : j);
+        const double aji_n = __shfl_sync(0xffffffffu, an, src_n);
+        const double ajk = __shfl_sync(0xffffffffu, a, src_k);
+        const double t = pn * a;                                     // FP64 #2
+        const double upd = fma(-aji_n, ajk, t);                      // FP64 #3
+        if (active && ei > j) a = upd;
+    }
+    // pivots p_j (in lanes (j, j)), their running scale sigma_j = prod_{k<j} p_k n_k, the test
+    double pj[6], pnj[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        pj[j] = __shfl_sync(0xffffffffu, a, idx(j, j));
+        pnj[j] = __shfl_sync(0xffffffffu, pn_mine, idx(j, j));
+    }
+    bool ok = true;
+    double sigma = 1.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double sj = exp2i(-(exponent_of(diag[j] + lam) >> 1));
+        ok = ok && pj[j] > 1e-12 * maxd * (sj * sj) * sigma;
+        sigma *= pnj[j];
+    }
+    if (!ok) return false;
+    // back-substitution on the rhs lanes (i, 6): x_k = c_k / p_k, c_i -= a_ik x_k
+    const double rcp = 1.0 / (ei == ek ? a : 1.0);        // lanes (k, k): 1 / p_k, all at once
+    double c = a;                                            // meaningful in lanes (i, 6)
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        const double rk = __shfl_sync(0xffffffffu, rcp, idx(k, k));
+        const double ck = __shfl_sync(0xffffffffu, c, idx(k, 6));
+        const double xk = ck * rk;
+        const double aik = __shfl_sync(0xffffffffu, a, idx(ei < k ? ei : k, k));
+        if (ek == 6 && ei < k) c = fma(-aik, xk, c);
+        if (ek == 6 && ei == k) c = xk;
+    }
+    if (active && ek == 6) xi[ei] = c * s_i;
+    __syncwarp();
+    return true;
+}
+
+// exp of the twist xi = (omega, upsilon) by one warp: R = I + A [w]x + B [w]x^2,
+// t = (I + B [w]x + C [w]x^2) u, A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3,
+// [w]x^2 = w w^T - th^2 I.  For th^2 < 0.01 lanes 0..2 evaluate the coefficients' Taylor series
+// in th^2 (truncation error < 1e-21); larger angles use sincos.  Lanes 0..8 then write R and
+// lanes 9..11 t into dT (row-major 3x4, shared); xi is in shared memory.
+__device__ void se3_exp_warp(const double* xi, double* dT) {
+    const int lane = threadIdx.x & 31;
+    const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double coef;
+    if (th2 < 1e-2) {
+        // coefficient tables of sum_k (-1)^k x^k / (2k+1)!, /(2k+2)!, /(2k+3)!
+        constexpr double kA[8] = {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880, -1.0 / 39916800,
+                                  1.0 / 6227020800.0, -1.0 / 1307674368000.0};
+        constexpr double kB[8] = {1.0 / 2, -1.0 / 24, 1.0 / 720, -1.0 / 40320, 1.0 / 3628800, -1.0 / 479001600,
+                                  1.0 / 87178291200.0, -1.0 / 20922789888000.0};
+        constexpr double kC[8] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800,
+                                  -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0};
+        coef = lane == 0 ? kA[7] : (lane == 1 ? kB[7] : kC[7]);
+#pragma unroll
+        for (int k = 6; k >= 0; --k) coef = (lane == 0 ? kA[k] : (lane == 1 ? kB[k] : kC[k])) + th2 * coef;
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        coef = lane == 0 ? sn / th : (lane == 1 ? (1.0 - cs) / th2 : (th - sn) / (th2 * th));
+    }
+    const double A = __shfl_sync(0xffffffffu, coef, 0);
+    const double B = __shfl_sync(0xffffffffu, coef, 1);
+    const double C = __shfl_sync(0xffffffffu, coef, 2);
+    // row r of [w]x and of w w^T - th2 I, held in registers for every r via selects
+    const int r = lane < 9 ? lane / 3 : (lane < 12 ? lane - 9 : 0);
+    const double wr = r == 0 ? w0 : (r == 1 ? w1 : w2);
+    const double K0 = r == 0 ? 0.0 : (r == 1 ? w2 : -w1);
+    const double K1 = r == 0 ? -w2 : (r == 1 ? 0.0 : w0);
+    const double K2 = r == 0 ? w1 : (r == 1 ? -w0 : 0.0);
+    const double Q0 = wr * w0 - (r == 0 ? th2 : 0.0);
+    const double Q1 = wr * w1 - (r == 1 ? th2 : 0.0);
+    const double Q2 = wr * w2 - (r == 2 ? th2 : 0.0);
+    if (lane < 9) {
+        const int cidx = lane - 3 * r;
+        const double Kc = cidx == 0 ? K0 : (cidx == 1 ? K1 : K2);
+        const double Qc = cidx == 0 ? Q0 : (cidx == 1 ? Q1 : Q2);
+        dT[4 * r + cidx] = ((r == cidx) ? 1.0 : 0.0) + A * Kc + B * Qc;
+    } else if (lane < 12) {
+        const double V0 = ((r == 0) ? 1.0 : 0.0) + B * K0 + C * Q0;
+        const double V1 = ((r == 1) ? 1.0 : 0.0) + B * K1 + C * Q1;
+        const double V2 = ((r == 2) ? 1.0 : 0.0) + B * K2 + C * Q2;
+        dT[4 * r + 3] = (V0 * xi[3] + V1 * xi[4]) + V2 * xi[5];
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------
+// exact fixed-point accumulation: a double x (|x| < 2^62) is rounded toward -inf to a multiple of
+// 2^-64 and held as a 128-bit two's-complement integer, split into four 32-bit chunks; chunk k is
+// added into 64-bit accumulator k.  Sums of up to 2^32 values are exact in any order.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void fx_add(unsigned long long* acc4, double x) {
+    const double fl = floor(x);
+    const long long hi = (long long)fl;
+    const unsigned long long lo = (unsigned long long)((x - fl) * 18446744073709551616.0);
+    const unsigned long long uhi = (unsigned long long)hi;
+    atomicAdd(acc4 + 0, lo & 0xffffffffull);
+    atomicAdd(acc4 + 1, lo >> 32);
+    atomicAdd(acc4 + 2, uhi & 0xffffffffull);
+    atomicAdd(acc4 + 3, uhi >> 32);
+}
+
+// value of a fixed-point number given its four (possibly carry-laden) 64-bit chunk sums
+__device__ __forceinline__ double fx_value(unsigned long long c0, unsigned long long c1,
+                                          unsigned long long c2, unsigned long long c3) {
+    // v = c0 + c1 2^32 + c2 2^64 + c3 2^96 (mod 2^128)
+    const unsigned long long lo_a = c0 + (c1 << 32);
+    const unsigned long long carry = (lo_a < c0) ? 1ull : 0ull;
+    const unsigned long long hi = (c1 >> 32) + c2 + (c3 << 32) + carry;
+    return (double)(long long)hi + (double)lo_a * 5.421010862427522e-20;  // lo * 2^-64
+}
+
+// Reduce-scatter of 32 per-lane values over a warp by butterfly exchange (31 shuffles instead of
+// 160): afterwards lane l holds the warp sum of value l.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int level = 0; level < 5; ++level) {
+        const int half = 16 >> level;
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float send = upper ? v[j] : v[j + half];
+            const float keep = upper ? v[j + half] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return v[0];
+}
+
+template <class Map>
+__global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
+track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, double* T_wc,
+             gsdf_track_stats* stats, Scratch sc) {
+    __shared__ float Rt[12];  // R (row-major) and t rounded once to FP32
+    __shared__ double Tsh[16];
+    __shared__ double part[kTrackWarps][32];
+    __shared__ double xi_sh[6], dT_sh[12];
+    __shared__ bool is_last;
+
+    if (threadIdx.x < 16) {
+        const double x = T_wc[threadIdx.x];
+        Tsh[threadIdx.x] = x;
+        if (threadIdx.x < 12) {
+            const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
+            Rt[c < 3 ? 3 * r + c : 9 + r] = __double2float_rn(x);
+        }
+    }
+    __syncthreads();
+    const float* R = Rt;
+    const float* t = Rt + 9;
+
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+
+    const int n_px = K.width * K.height;
+    const float delta = prm.huber;
+    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x) {
+        const float D = __ldg(depth + pix);
+        if (!depth_ok(D, K.depth_max)) continue;
+        const int v = pix / K.width;
+        const int u = pix - v * K.width;
+        float p[3], P[3];
+        backproject(K, u, v, D, p);
+        xform(R, t, p, P);
+        const int mx = round_voxel(P[0], prm.inv_vs);
+        const int my = round_voxel(P[1], prm.inv_vs);
+        const int mz = round_voxel(P[2], prm.inv_vs);
+        const long long idx = map.find(mx, my, mz);
+        if (idx < 0) continue;
+        const float W = __ldg(map.W + idx);
+        if (!(W > 0.0f)) continue;
+        const float4 a = __ldg(map.A + idx);
+        const float gn2 = a.y * a.y + a.z * a.z + a.w * a.w;
+        if (!(gn2 > 0.0f)) continue;
+        const float inv_gn = rsqrtf(gn2);
+        const float gx = a.y * inv_gn, gy = a.z * inv_gn, gz = a.w * inv_gn;
+        const float psi = __fdividef(a.x, W);
+        // P - v_s m with a single rounding per component
+        const float dx = fmaf(-(float)mx, prm.vs, P[0]);
+        const float dy = fmaf(-(float)my, prm.vs, P[1]);
+        const float dz = fmaf(-(float)mz, prm.vs, P[2]);
+        const float r = psi + (gx * dx + gy * dy + gz * dz);
+        const float J[6] = {P[1] * gz - P[2] * gy, P[2] * gx - P[0] * gz, P[0] * gy - P[1] * gx,
+                            gx, gy, gz};
+        const float ar = fabsf(r);
+        const float w = ar <= delta ? 1.0f : __fdividef(delta, ar);
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const float wJi = w * J[i];
+#pragma unroll
+            for (int j = i; j < 6; ++j) acc[q++] += wJi * J[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[21 + i] += w * J[i] * r;
+        acc[27] += w * r * r;
+        acc[28] += 1.0f;
+        acc[29] += ar > delta ? 1.0f : 0.0f;
+    }
+
+    // warp: reduce-scatter (lane l <- term l); block: fixed tree over warps in FP64
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    part[warp][lane] = (double)warp_reduce_scatter32(acc);
+    __syncthreads();
+#pragma unroll
+    for (int h = kTrackWarps / 2; h > 0; h >>= 1) {
+        if (warp < h) part[warp][lane] += part[warp + h][lane];
+        __syncthreads();
+    }
+    // block b adds into accumulator copy b mod kAccumCopies (spreads same-address atomics)
+    if (threadIdx.x < kTerms)
+        fx_add(sc.accum + ((blockIdx.x % kAccumCopies) * 32 + threadIdx.x) * 4, part[0][threadIdx.x]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(sc.counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+
+    // Last block: warp w reads copy w (lane = term), the copies are added with a fixed integer
+    // tree (exact), and the accumulators are cleared for the next launch.
+    __threadfence();
+    __shared__ unsigned long long csum[kAccumCopies][32][4];
+    {
+        unsigned long long* src = sc.accum + ((size_t)warp * 32 + lane) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            csum[warp][lane][q] = __ldcg(src + q);
+            src[q] = 0ull;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = kAccumCopies / 2; h > 0; h >>= 1) {
+        if (warp < h) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) csum[warp][lane][q] += csum[warp + h][lane][q];
+        }
+        __syncthreads();
+    }
+    if (warp == 0) part[0][lane] = lane < kTerms ? fx_value(csum[0][lane][0], csum[0][lane][1], csum[0][lane][2], csum[0][lane][3]) : 0.0;
+    __syncwarp();
+    if (warp != 0) return;
+    const double* total = part[0];
+    if (lane == 0) *sc.counter = 0u;
+    const long long n_valid = (long long)(total[28] + 0.5);
+    const bool ok = solve6_warp(total, prm.damping, n_valid, xi_sh);
+    if (ok) se3_exp_warp(xi_sh, dT_sh);
+    // T <- dT * T: lanes 0..11 compute one entry each of the top three rows
+    if (ok && lane < 12) {
+        const int i = lane >> 2, j = lane & 3;
+        double tn = (dT_sh[4 * i + 0] * Tsh[j] + dT_sh[4 * i + 1] * Tsh[4 + j]) + dT_sh[4 * i + 2] * Tsh[8 + j];
+        if (j == 3) tn += dT_sh[4 * i + 3];
+        T_wc[lane] = tn;
+    }
+    if (stats) {
+        if (lane < 21) stats->H[lane] = total[lane];
+        else if (lane < 27) stats->b[lane - 21] = total[lane];
+        if (lane < 6) stats->xi[lane] = ok ? xi_sh[lane] : 0.0;
+        if (lane == 0) {
+            stats->energy = total[27];
+            stats->n_valid = n_valid;
+            stats->n_huber = (long long)(total[29] + 0.5);
+            stats->status = ok ? (int)GSDF_OK : (int)GSDF_ERR_DEGENERATE;
+            stats->pad = 0;
+        }
+    }
+}
+
+cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
+                         const Params& prm, double* T_wc, gsdf_track_stats* stats,
+                         const Scratch& sc, int num_sms, cudaStream_t st) {
+    const long long n_px = (long long)K.width * K.height;
+    long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
+    long long cap = (long long)kTrackBlocksPerSM * num_sms;
+    if (cap > sc.max_track_blocks) cap = sc.max_track_blocks;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (dm)
+        track_kernel<DenseMap><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*dm, depth, K, prm, T_wc, stats, sc);
+    else
+        track_kernel<HashMap><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*hm, depth, K, prm, T_wc, stats, sc);
+    return cudaGetLastError();
+}
+
+}  // namespace gsdf

@@ -1,0 +1,283 @@
+"""Python binding of libgsdf (include/gsdf.h): argument marshalling only.
+
+Every C entry point is exposed under its own name (gsdf_create, gsdf_integrate, ...); `Map` wraps
+a handle for convenience.  PyTorch supplies device memory and streams: depth images, poses and
+statistics are torch CUDA tensors whose data pointers are passed straight to the library.  All
+computation runs in the library's CUDA kernels; if the library cannot be loaded this module
+raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GSDF_OK = 0
+GSDF_ERR_INVALID_ARG = 1
+GSDF_ERR_CUDA = 2
+GSDF_ERR_OOM = 3
+GSDF_ERR_CAPACITY = 4
+GSDF_ERR_DEGENERATE = 5
+GSDF_ERR_TIMEOUT = 6
+GSDF_ERR_NO_VALID_PIXELS = 7
+GSDF_GRID_DENSE = 0
+GSDF_GRID_HASHED = 1
+
+
+class gsdf_intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("depth_max", C.c_float)]
+
+
+class gsdf_config(C.Structure):
+    _fields_ = [("grid_kind", C.c_int32), ("dense_dims", C.c_int32 * 3), ("dense_origin", C.c_int32 * 3),
+                ("voxel_size", C.c_float), ("truncation", C.c_float), ("weight_eps", C.c_float),
+                ("huber_delta", C.c_float), ("cos_max_angle", C.c_float), ("damping", C.c_double),
+                ("hash_slots", C.c_int64), ("max_probe", C.c_int32), ("reserved", C.c_int32)]
+
+
+class gsdf_track_stats(C.Structure):
+    _fields_ = [("H", C.c_double * 21), ("b", C.c_double * 6), ("energy", C.c_double),
+                ("n_valid", C.c_int64), ("n_huber", C.c_int64), ("status", C.c_int32), ("pad", C.c_int32),
+                ("xi", C.c_double * 6)]
+
+
+class gsdf_integrate_stats(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("n_visits", C.c_int64), ("n_blocks_new", C.c_int64),
+                ("n_blocks_total", C.c_int64)]
+
+
+class gsdf_voxel(C.Structure):
+    _fields_ = [("m", C.c_int32 * 3), ("psi", C.c_float), ("g", C.c_float * 3), ("w", C.c_float)]
+
+
+VOXEL_DTYPE = np.dtype([("m", "<i4", 3), ("psi", "<f4"), ("g", "<f4", 3), ("w", "<f4")])
+TRACK_STATS_BYTES = C.sizeof(gsdf_track_stats)
+INTEGRATE_STATS_BYTES = C.sizeof(gsdf_integrate_stats)
+
+# every entry point declared in include/gsdf.h, with (restype, argtypes)
+_P = C.POINTER
+_SIGS = {
+    "gsdf_create": (C.c_int, [_P(gsdf_config), C.c_void_p, _P(C.c_void_p)]),
+    "gsdf_destroy": (C.c_int, [C.c_void_p]),
+    "gsdf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gsdf_upload_dense": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gsdf_integrate": (C.c_int, [C.c_void_p, C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p]),
+    "gsdf_track_step": (C.c_int, [C.c_void_p, C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p]),
+    "gsdf_track": (C.c_int, [C.c_void_p, C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_int32, C.c_void_p]),
+    "gsdf_extract_voxels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
+    "gsdf_load_voxels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "gsdf_num_blocks": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
+    "gsdf_sync": (C.c_int, [C.c_void_p]),
+    "gsdf_status_string": (C.c_char_p, [C.c_int]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libgsdf.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if path is None:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgsdf not found at {path}")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GsdfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {load_library().gsdf_status_string(status).decode()} (status {status})")
+
+
+def _check(status: int, where: str):
+    if status != GSDF_OK:
+        raise GsdfError(status, where)
+
+
+# -------------------------------------------------------------------------------------------
+# thin wrappers with the C names
+# -------------------------------------------------------------------------------------------
+
+
+def gsdf_create(cfg: gsdf_config, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load_library().gsdf_create(C.byref(cfg), C.c_void_p(stream), C.byref(h)), "gsdf_create")
+    return h.value
+
+
+def gsdf_destroy(h: int) -> int:
+    return load_library().gsdf_destroy(C.c_void_p(h))
+
+
+def gsdf_set_stream(h: int, stream: int) -> int:
+    return load_library().gsdf_set_stream(C.c_void_p(h), C.c_void_p(stream))
+
+
+def gsdf_upload_dense(h: int, psi: np.ndarray, g: np.ndarray, w: np.ndarray) -> int:
+    psi = np.ascontiguousarray(psi, np.float32)
+    g = np.ascontiguousarray(g, np.float32)
+    w = np.ascontiguousarray(w, np.float32)
+    return load_library().gsdf_upload_dense(C.c_void_p(h), psi.ctypes.data, g.ctypes.data, w.ctypes.data)
+
+
+def gsdf_integrate(h: int, depth_ptr: int, K: gsdf_intrinsics, pose_ptr: int, stats_ptr: int = 0) -> int:
+    return load_library().gsdf_integrate(C.c_void_p(h), C.c_void_p(depth_ptr), C.byref(K), C.c_void_p(pose_ptr),
+                                         C.c_void_p(stats_ptr or None))
+
+
+def gsdf_track_step(h: int, depth_ptr: int, K: gsdf_intrinsics, pose_ptr: int, stats_ptr: int = 0) -> int:
+    return load_library().gsdf_track_step(C.c_void_p(h), C.c_void_p(depth_ptr), C.byref(K), C.c_void_p(pose_ptr),
+                                          C.c_void_p(stats_ptr or None))
+
+
+def gsdf_track(h: int, depth_ptr: int, K: gsdf_intrinsics, pose_ptr: int, n_iters: int, stats_ptr: int = 0) -> int:
+    return load_library().gsdf_track(C.c_void_p(h), C.c_void_p(depth_ptr), C.byref(K), C.c_void_p(pose_ptr),
+                                     n_iters, C.c_void_p(stats_ptr or None))
+
+
+def gsdf_extract_voxels(h: int, out: np.ndarray | None, capacity: int):
+    n = C.c_size_t()
+    ptr = out.ctypes.data if out is not None else None
+    st = load_library().gsdf_extract_voxels(C.c_void_p(h), C.c_void_p(ptr), capacity, C.byref(n))
+    return st, n.value
+
+
+def gsdf_load_voxels(h: int, vox: np.ndarray) -> int:
+    vox = np.ascontiguousarray(vox, VOXEL_DTYPE)
+    return load_library().gsdf_load_voxels(C.c_void_p(h), C.c_void_p(vox.ctypes.data), len(vox))
+
+
+def gsdf_num_blocks(h: int) -> int:
+    n = C.c_int64()
+    _check(load_library().gsdf_num_blocks(C.c_void_p(h), C.byref(n)), "gsdf_num_blocks")
+    return n.value
+
+
+def gsdf_sync(h: int) -> int:
+    return load_library().gsdf_sync(C.c_void_p(h))
+
+
+def gsdf_status_string(s: int) -> str:
+    return load_library().gsdf_status_string(s).decode()
+
+
+# -------------------------------------------------------------------------------------------
+# convenience
+# -------------------------------------------------------------------------------------------
+
+
+def intrinsics(cam) -> gsdf_intrinsics:
+    return gsdf_intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.depth_max)
+
+
+def make_config(voxel_size, *, dense_dims=None, dense_origin=(0, 0, 0), truncation=None, weight_eps=None,
+                huber_delta=None, cos_max_angle=0.25881904, damping=0.0, hash_slots=1 << 16,
+                max_probe=128) -> gsdf_config:
+    vs = float(voxel_size)
+    c = gsdf_config()
+    c.grid_kind = GSDF_GRID_HASHED if dense_dims is None else GSDF_GRID_DENSE
+    if dense_dims is not None:
+        c.dense_dims[:] = list(dense_dims)
+        c.dense_origin[:] = list(dense_origin)
+    c.voxel_size = vs
+    c.truncation = 5 * vs if truncation is None else truncation
+    c.weight_eps = vs if weight_eps is None else weight_eps
+    c.huber_delta = vs if huber_delta is None else huber_delta
+    c.cos_max_angle = cos_max_angle
+    c.damping = damping
+    c.hash_slots = hash_slots
+    c.max_probe = max_probe
+    return c
+
+
+def track_stats_from_bytes(buf) -> gsdf_track_stats:
+    b = bytes(np.asarray(buf, np.uint8).tobytes())
+    return gsdf_track_stats.from_buffer_copy(b[:TRACK_STATS_BYTES])
+
+
+def integrate_stats_from_bytes(buf) -> gsdf_integrate_stats:
+    b = bytes(np.asarray(buf, np.uint8).tobytes())
+    return gsdf_integrate_stats.from_buffer_copy(b[:INTEGRATE_STATS_BYTES])
+
+
+class Map:
+    """A gsdf map on the current CUDA device, issuing work on a torch stream.
+
+    Device buffers (depth, pose, statistics) are torch CUDA tensors owned by the caller."""
+
+    def __init__(self, cfg: gsdf_config, stream=None):
+        import torch
+
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.cfg = cfg
+        self.h = gsdf_create(cfg, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gsdf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload_dense(self, psi, g, w):
+        _check(gsdf_upload_dense(self.h, psi, g, w), "gsdf_upload_dense")
+
+    def integrate(self, depth, K: gsdf_intrinsics, pose, stats=None):
+        _check(gsdf_integrate(self.h, depth.data_ptr(), K, pose.data_ptr(), stats.data_ptr() if stats is not None else 0),
+               "gsdf_integrate")
+
+    def track_step(self, depth, K: gsdf_intrinsics, pose, stats=None):
+        _check(gsdf_track_step(self.h, depth.data_ptr(), K, pose.data_ptr(), stats.data_ptr() if stats is not None else 0),
+               "gsdf_track_step")
+
+    def track(self, depth, K: gsdf_intrinsics, pose, n_iters: int, stats=None):
+        """n_iters Gauss-Newton steps (replayed from a cached CUDA graph); stats: None or a
+        device uint8 tensor of n_iters * TRACK_STATS_BYTES."""
+        _check(gsdf_track(self.h, depth.data_ptr(), K, pose.data_ptr(), n_iters,
+                          stats.data_ptr() if stats is not None else 0), "gsdf_track")
+
+    def new_track_stats(self, n: int | None = None):
+        if n is not None:
+            return self.torch.zeros((n, TRACK_STATS_BYTES), dtype=self.torch.uint8, device="cuda")
+        return self.torch.zeros(TRACK_STATS_BYTES, dtype=self.torch.uint8, device="cuda")
+
+    def new_integrate_stats(self):
+        return self.torch.zeros(INTEGRATE_STATS_BYTES, dtype=self.torch.uint8, device="cuda")
+
+    def sync(self):
+        _check(gsdf_sync(self.h), "gsdf_sync")
+
+    def num_blocks(self) -> int:
+        return gsdf_num_blocks(self.h)
+
+    def extract(self) -> np.ndarray:
+        """All voxels with W > 0 as a structured array (m, psi, g, w), in the library's order."""
+        st, n = gsdf_extract_voxels(self.h, None, 0)
+        if st not in (GSDF_OK, GSDF_ERR_CAPACITY):
+            _check(st, "gsdf_extract_voxels")
+        out = np.zeros(n, VOXEL_DTYPE)
+        if n:
+            st, n2 = gsdf_extract_voxels(self.h, out, n)
+            _check(st, "gsdf_extract_voxels")
+            assert n2 == n
+        return out
+
+    def load(self, vox: np.ndarray):
+        _check(gsdf_load_voxels(self.h, vox), "gsdf_load_voxels")

@@ -333,7 +333,9 @@ def room_trajectory(scene: RoomScene, n_frames: int, seed: int, frames_per_segme
 
     Positions stay >= 0.35 m from every surface and >= 0.7 m from the walls; about step /
     frames_per_segment metres of motion per frame (2 cm at the defaults)."""
+    # separate streams for positions and targets: the first frames do not depend on n_frames
     rng = np.random.default_rng(seed + 7919)
+    rng_t = np.random.default_rng(seed + 7920)
     n_ctrl = n_frames // frames_per_segment + 4
     center = 0.5 * (scene.lo + scene.hi)
     pos = [center.copy()]
@@ -351,9 +353,9 @@ def room_trajectory(scene: RoomScene, n_frames: int, seed: int, frames_per_segme
             if tries > 200:  # back off toward the centre
                 pos.append(0.5 * (pos[-1] + center))
     pos = np.array(pos)
-    tgt = [center + rng.uniform(-1, 1, size=3) * np.array([1.2, 1.2, 0.6])]
+    tgt = [center + rng_t.uniform(-1, 1, size=3) * np.array([1.2, 1.2, 0.6])]
     while len(tgt) < n_ctrl:
-        tgt.append(np.clip(tgt[-1] + 0.6 * _unit(rng.normal(size=3)), scene.lo + 0.2, scene.hi - 0.2))
+        tgt.append(np.clip(tgt[-1] + 0.6 * _unit(rng_t.normal(size=3)), scene.lo + 0.2, scene.hi - 0.2))
     tgt = np.array(tgt)
     s = np.arange(n_frames, dtype=np.float64) / frames_per_segment
     P = _bspline(pos, s)
