@@ -200,6 +200,38 @@ gsdf_status gsdf_num_blocks(gsdf_handle* h, int64_t* n_out);
 /* Wait for the handle's stream; return (and clear) the first device-detected error. */
 gsdf_status gsdf_sync(gsdf_handle* h);
 
+/* Allocation-free tracking step (the paper has no counterpart; this is a deployment aid).
+ * For callers that cannot call cudaMalloc -- code confined to a device-memory budget that a host
+ * framework owns and hands out, or a real-time loop where an allocation, and the device-wide
+ * synchronisation it may cause, is not allowed -- this entry point performs exactly one
+ * gsdf_track_step on a dense grid that the caller owns, without a handle and without allocating
+ * anything.  The caller passes every input and output:
+ *   depth_dev   H*W FP32 depth (device), as for gsdf_track_step;
+ *   A_dev       dims[0]*dims[1]*dims[2] float4 (device), x fastest: (W psi, g.x, g.y, g.z) of each
+ *               voxel -- the library's own dense payload layout (psi times its weight, then the
+ *               unnormalised gradient);
+ *   W_dev       the matching weights (device); W = 0 marks an unobserved voxel;
+ *   dims/origin grid size and integer coordinate of voxel (0,0,0) (host arrays of 3);
+ *   voxel_size, huber_delta, damping: as in gsdf_config;
+ *   T_wc_dev    pose, read and updated (device); stats_dev: NULL or device gsdf_track_stats;
+ *   cuda_stream the stream to launch on (NULL = legacy default stream).
+ * Scratch: a 16,640-byte array in the library's device memory (a static __device__ array that
+ * every GPU which loads the library holds until the process exits).  The scratch this step
+ * needs does not grow with the image or grid size; a request needing more than the array holds
+ * would return GSDF_ERR_CAPACITY.  Inputs beyond the limits gsdf_create and gsdf_track_step
+ * accept (image sides > 32768, grid sides > 65536) return GSDF_ERR_INVALID_ARG.
+ * The first call on a device resolves the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call clears the
+ * array's accumulators on cuda_stream before using them, and all calls share the one array:
+ * calls that may overlap on the GPU (different streams, or the same call issued into several
+ * concurrently running graphs) race with each other and must be serialised by the caller. */
+gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, const gsdf_intrinsics* K,
+                                          const void* A_dev, const float* W_dev,
+                                          const int32_t dims[3], const int32_t origin[3],
+                                          float voxel_size, float huber_delta, double damping,
+                                          double* T_wc_dev, gsdf_track_stats* stats_dev,
+                                          void* cuda_stream);
+
 /* Static description of a status code. */
 const char* gsdf_status_string(gsdf_status s);
 

@@ -397,3 +397,113 @@ cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* dep
 }
 
 }  // namespace gsdf
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free tracking step.
+//
+// Some callers cannot call cudaMalloc: code that must run inside a fixed device-memory budget
+// handed to it by a host framework (which owns every allocation), or a real-time loop in which
+// an allocation, with the device-wide synchronisation it may imply, is not allowed.  For them
+// gsdf_track_step_dense_noalloc runs the tracking kernel above on a caller-owned dense grid and
+// takes its scratch (the fixed-point accumulators and the last-block ticket) from a file-scope
+// device array instead of a handle's allocations.
+// ------------------------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace gsdf {
+namespace {
+
+// kAccumWords accumulator words, then one word for the ticket counter, padded: 16640 bytes.
+constexpr size_t kStaticScratchWords = kAccumWords + 32;
+constexpr size_t kStaticScratchNeeded = kAccumWords + 1;
+static_assert(kStaticScratchNeeded <= kStaticScratchWords, "static scratch too small");
+static __device__ __align__(256) unsigned long long g_static_scratch[kStaticScratchWords];
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+unsigned long long* g_static_ptr[kMaxStaticDevices];  // device address of the array, per device
+int g_static_sms[kMaxStaticDevices];
+
+bool finite_positive(float x) { return isfinite(x) && x > 0.0f; }
+
+}  // namespace
+}  // namespace gsdf
+
+extern "C" gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, const gsdf_intrinsics* K,
+                                                     const void* A_dev, const float* W_dev,
+                                                     const int32_t dims[3], const int32_t origin[3],
+                                                     float voxel_size, float huber_delta, double damping,
+                                                     double* T_wc_dev, gsdf_track_stats* stats_dev,
+                                                     void* cuda_stream) {
+    using namespace gsdf;
+    if (!depth_dev || !K || !A_dev || !W_dev || !dims || !origin || !T_wc_dev) return GSDF_ERR_INVALID_ARG;
+    if (!finite_positive(voxel_size) || !finite_positive(huber_delta) || !isfinite(damping) || damping < 0.0)
+        return GSDF_ERR_INVALID_ARG;
+    if (!finite_positive(K->fx) || !finite_positive(K->fy) || !isfinite(K->cx) || !isfinite(K->cy) ||
+        K->width <= 0 || K->height <= 0 || K->width > 32768 || K->height > 32768 || !finite_positive(K->depth_max))
+        return GSDF_ERR_INVALID_ARG;
+    long long n = 1;
+    for (int i = 0; i < 3; ++i) {
+        if (dims[i] <= 0 || dims[i] > (1 << 16)) return GSDF_ERR_INVALID_ARG;
+        n *= dims[i];
+        if ((long long)origin[i] < -(1ll << 23) || (long long)origin[i] + dims[i] > (1ll << 23)) return GSDF_ERR_INVALID_ARG;
+    }
+    if (n > (1ll << 34)) return GSDF_ERR_INVALID_ARG;
+    // the scratch this call needs must fit the static array (it does not depend on the input
+    // sizes: the accumulators are replicated a fixed number of times)
+    if (kStaticScratchNeeded > kStaticScratchWords) return GSDF_ERR_CAPACITY;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GSDF_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxStaticDevices) return GSDF_ERR_INVALID_ARG;
+    unsigned long long* scratch = nullptr;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_ptr[dev]) {  // once per device, with that device current
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return GSDF_ERR_CUDA;
+            int count = 0;
+            if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GSDF_ERR_CUDA;
+            g_static_ptr[dev] = (unsigned long long*)p;
+            g_static_sms[dev] = count;
+        }
+        scratch = g_static_ptr[dev];
+        sms = g_static_sms[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the array keeps the previous call's contents: clear the accumulators and the ticket
+    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * kStaticScratchNeeded, st) != cudaSuccess)
+        return GSDF_ERR_CUDA;
+
+    DenseMap dm;
+    dm.A = (float4*)const_cast<void*>(A_dev);
+    dm.W = const_cast<float*>(W_dev);
+    for (int i = 0; i < 3; ++i) {
+        dm.dims[i] = dims[i];
+        dm.origin[i] = origin[i];
+    }
+    Intr ki;
+    ki.fx = K->fx;
+    ki.fy = K->fy;
+    ki.cx = K->cx;
+    ki.cy = K->cy;
+    ki.width = K->width;
+    ki.height = K->height;
+    ki.depth_max = K->depth_max;
+    ki.ifx = (float)(1.0 / (double)K->fx);
+    ki.ify = (float)(1.0 / (double)K->fy);
+    Params prm = {};
+    prm.vs = voxel_size;
+    prm.inv_vs = (float)(1.0 / (double)voxel_size);
+    prm.huber = huber_delta;
+    prm.damping = damping;
+    Scratch sc = {};
+    sc.accum = scratch;
+    sc.counter = (unsigned int*)(scratch + kAccumWords);
+    sc.max_track_blocks = 2 * sms;
+    const cudaError_t e = launch_track(&dm, nullptr, depth_dev, ki, prm, T_wc_dev, stats_dev, sc, sms, st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GSDF_ERR_OOM : GSDF_ERR_CUDA;
+    return GSDF_OK;
+}

@@ -73,6 +73,9 @@ _SIGS = {
     "gsdf_num_blocks": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "gsdf_sync": (C.c_int, [C.c_void_p]),
     "gsdf_status_string": (C.c_char_p, [C.c_int]),
+    "gsdf_track_step_dense_noalloc": (C.c_int, [C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p,
+                                                _P(C.c_int32), _P(C.c_int32), C.c_float, C.c_float, C.c_double,
+                                                C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -167,6 +170,17 @@ def gsdf_num_blocks(h: int) -> int:
 
 def gsdf_sync(h: int) -> int:
     return load_library().gsdf_sync(C.c_void_p(h))
+
+
+def gsdf_track_step_dense_noalloc(depth_ptr: int, K: gsdf_intrinsics, A_ptr: int, W_ptr: int, dims, origin,
+                                  voxel_size: float, huber_delta: float, damping: float, pose_ptr: int,
+                                  stats_ptr: int = 0, stream: int = 0) -> int:
+    """One tracking step on a caller-owned dense grid; allocates nothing (see include/gsdf.h)."""
+    d = (C.c_int32 * 3)(*dims)
+    o = (C.c_int32 * 3)(*origin)
+    return load_library().gsdf_track_step_dense_noalloc(
+        C.c_void_p(depth_ptr), C.byref(K), C.c_void_p(A_ptr), C.c_void_p(W_ptr), d, o, voxel_size, huber_delta,
+        damping, C.c_void_p(pose_ptr), C.c_void_p(stats_ptr or None), C.c_void_p(stream or None))
 
 
 def gsdf_status_string(s: int) -> str:
