@@ -198,18 +198,6 @@ static void orc_round_pose(const double T[16], orc_pose32* q) {
     }
 }
 
-/* P = ((R_i0 p0 + R_i1 p1) + R_i2 p2) + t_i, each operation rounded to FP32 */
-static void orc_xform32(const float R[9], const float t[3], const float p[3], float P[3]) {
-    for (int i = 0; i < 3; ++i) {
-        float a = R[3 * i + 0] * p[0];
-        float b = R[3 * i + 1] * p[1];
-        float c = R[3 * i + 2] * p[2];
-        float s = a + b;
-        s = s + c;
-        P[i] = s + t[i];
-    }
-}
-
 /* j* of Eq. (taylor): nearest grid voxel, m = floor(P / v_s + 1/2) with 1/v_s rounded to FP32 */
 static void orc_round_voxel(const float P[3], float inv_vs, int32_t m[3]) {
     for (int i = 0; i < 3; ++i) {
@@ -242,14 +230,35 @@ static void orc_backproject(const orc_intrinsics* K, const orc_recip* rc, int u,
     p[2] = z;
 }
 
+/* world direction of pixel (u, v): d = R ray, ray = ((u - cx)/fx, (v - cy)/fy, 1);
+ * d_i = (R_i0 ray_0 + R_i1 ray_1) + R_i2, each operation rounded to FP32 */
+static void orc_ray_world(const orc_intrinsics* K, const orc_recip* rc, const float R[9], int u, int v, float d[3]) {
+    float xn = ((float)u - K->cx) * rc->ifx;
+    float yn = ((float)v - K->cy) * rc->ify;
+    for (int i = 0; i < 3; ++i) {
+        float a = R[3 * i + 0] * xn;
+        float b = R[3 * i + 1] * yn;
+        float s = a + b;
+        d[i] = s + R[3 * i + 2];
+    }
+}
+
+/* world point at depth z along that ray: P_i = z d_i + t_i (product, then sum, in FP32) */
+static void orc_ray_point(const float d[3], const float t[3], float z, float P[3]) {
+    for (int i = 0; i < 3; ++i) {
+        float a = z * d[i];
+        P[i] = a + t[i];
+    }
+}
+
 void orc_pixel_point(const orc_intrinsics* K, const double T_wc[16], int u, int v, float D,
                      float P_out[3], int32_t m_out[3], float voxel_size) {
     orc_pose32 q;
     orc_round_pose(T_wc, &q);
     orc_recip rc = orc_recips(K, voxel_size);
-    float p[3];
-    orc_backproject(K, &rc, u, v, D, p);
-    orc_xform32(q.R, q.t, p, P_out);
+    float d[3];
+    orc_ray_world(K, &rc, q.R, u, v, d);
+    orc_ray_point(d, q.t, D, P_out);
     orc_round_voxel(P_out, rc.inv_vs, m_out);
 }
 
@@ -344,14 +353,15 @@ int orc_integrate(orc_map* map, const float* depth, const orc_intrinsics* K, con
             double nw[3];
             for (int i = 0; i < 3; ++i)
                 nw[i] = (double)q.R[3 * i] * n[0] + (double)q.R[3 * i + 1] * n[1] + (double)q.R[3 * i + 2] * n[2];
+            float dw[3];
+            orc_ray_world(K, &rc, q.R, u, v, dw);
             int32_t prev[3] = {0, 0, 0};
             int have_prev = 0;
             for (int k = 0; k <= 2 * Kb; ++k) {
                 float step = (float)(k - Kb) * h;
                 float z = D + step;
-                float p[3], P[3];
-                orc_backproject(K, &rc, u, v, z, p);
-                orc_xform32(q.R, q.t, p, P);
+                float P[3];
+                orc_ray_point(dw, q.t, z, P);
                 int32_t m[3];
                 orc_round_voxel(P, rc.inv_vs, m);
                 if (have_prev && m[0] == prev[0] && m[1] == prev[1] && m[2] == prev[2]) continue;
@@ -423,10 +433,10 @@ int orc_track_reduce(const orc_map* map, const float* depth, const orc_intrinsic
         for (int u = 0; u < K->width; ++u) {
             const float D = depth[(size_t)v * K->width + u];
             if (!orc_depth_ok(D, K->depth_max)) continue;
-            float p[3], Pf[3];
+            float dw[3], Pf[3];
             int32_t m[3];
-            orc_backproject(K, &rc, u, v, D, p);
-            orc_xform32(q.R, q.t, p, Pf);
+            orc_ray_world(K, &rc, q.R, u, v, dw);
+            orc_ray_point(dw, q.t, D, Pf);
             orc_round_voxel(Pf, rc.inv_vs, m);
             double P[3] = {Pf[0], Pf[1], Pf[2]}, gh[3], r;
             if (orc_taylor(map, P, m, &r, gh) != 0) continue;

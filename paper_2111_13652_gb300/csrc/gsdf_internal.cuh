@@ -174,10 +174,16 @@ __device__ __forceinline__ float dot_row(const float* r, const float p[3]) {
     return __fadd_rn(s, __fmul_rn(r[2], p[2]));
 }
 
-__device__ __forceinline__ void xform(const float* R, const float* t, const float p[3], float P[3]) {
+// World direction of pixel (u, v): d = R ray, ray = ((u - cx)/fx, (v - cy)/fy, 1),
+// d_i = (R_i0 ray_0 + R_i1 ray_1) + R_i2.  The world point at depth z is P_i = z d_i + t_i.
+__device__ __forceinline__ void ray_world(const Intr& K, const float* R, int u, int v, float d[3]) {
+    const float xn = __fmul_rn(__fsub_rn((float)u, K.cx), K.ifx);
+    const float yn = __fmul_rn(__fsub_rn((float)v, K.cy), K.ify);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) P[i] = __fadd_rn(dot_row(R + 3 * i, p), t[i]);
+    for (int i = 0; i < 3; ++i) d[i] = __fadd_rn(__fadd_rn(__fmul_rn(R[3 * i], xn), __fmul_rn(R[3 * i + 1], yn)), R[3 * i + 2]);
 }
+
+__device__ __forceinline__ float ray_coord(float z, float d, float t) { return __fadd_rn(__fmul_rn(z, d), t); }
 
 __device__ __forceinline__ int round_voxel(float x, float inv_vs) {
     return (int)floorf(__fadd_rn(__fmul_rn(x, inv_vs), 0.5f));

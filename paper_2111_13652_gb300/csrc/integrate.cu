@@ -3,11 +3,14 @@
 // distance"), with block allocation fused in (hashed maps allocate the block of every voxel
 // that receives an update).
 //
-// One thread per pixel: the FP32 index path decides validity, the normal and its 75 degree
-// test, the ray samples' voxels and the band test exactly as specified; each distinct voxel of
-// the ray then receives (w d, w n_w) with one 16-byte vector atomic and w with one scalar
+// One thread per pixel.  The FP32 index path decides validity, the normal and its 75 degree test,
+// the voxels of the ray's samples and the band test, exactly as specified; the world point of a
+// sample at depth z is t + z (R ray), with the rotated ray formed once per pixel.  Each distinct
+// voxel of the ray then receives (w d, w n_w) with one 16-byte vector atomic and w with one scalar
 // atomic.  Because the payload stores W psi, the per-voxel sums equal the sequential running
-// average of Eq. (sdf_update) up to summation order.
+// average of Eq. (sdf_update) up to summation order.  The loop runs over distinct voxels, not
+// samples, so the lanes of a warp stay converged on the expensive visit body, and the last block
+// looked up is cached per ray.
 #include "gsdf_internal.cuh"
 
 namespace gsdf {
@@ -58,6 +61,37 @@ __device__ __forceinline__ bool pixel_normal(const float* __restrict__ depth, co
     return c >= prm.cos_max;
 }
 
+// Per-ray cache of the last block looked up: consecutive voxels of a ray mostly share a block.
+struct BlockCache {
+    int bx = 0x7fffffff, by = 0, bz = 0;
+    long long base = -1;  // payload index of local voxel 0, or -1 when the block is unusable
+};
+
+template <class Map>
+__device__ __forceinline__ long long voxel_index(const Map& map, int mx, int my, int mz, BlockCache& bc,
+                                                 int* err, unsigned int* n_new);
+
+template <>
+__device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, int mx, int my, int mz, BlockCache& bc,
+                                                          int* err, unsigned int* n_new) {
+    const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
+    if (bx != bc.bx || by != bc.by || bz != bc.bz) {
+        const long long idx = map.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
+        bc.bx = bx;
+        bc.by = by;
+        bc.bz = bz;
+        bc.base = idx;
+    }
+    if (bc.base < 0) return -1;
+    return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
+}
+
+template <>
+__device__ __forceinline__ long long voxel_index<DenseMap>(const DenseMap& map, int mx, int my, int mz, BlockCache&,
+                                                           int*, unsigned int*) {
+    return map.find(mx, my, mz);
+}
+
 template <class Map>
 __global__ void __launch_bounds__(kIntThreads)
 integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
@@ -86,24 +120,33 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
         const float nwx = pose.R[0] * n[0] + pose.R[1] * n[1] + pose.R[2] * n[2];
         const float nwy = pose.R[3] * n[0] + pose.R[4] * n[1] + pose.R[5] * n[2];
         const float nwz = pose.R[6] * n[0] + pose.R[7] * n[1] + pose.R[8] * n[2];
-        const float xn = __fmul_rn(__fsub_rn((float)u, K.cx), K.ifx);
-        const float yn = __fmul_rn(__fsub_rn((float)v, K.cy), K.ify);
-        int pmx = 0, pmy = 0, pmz = 0;
-        bool have_prev = false;
+        float dw[3];
+        ray_world(K, pose.R, u, v, dw);
         const int Kb = prm.band_half;
-        for (int k = 0; k <= 2 * Kb; ++k) {
-            const float z = __fadd_rn(D, __fmul_rn((float)(k - Kb), prm.half_vs));
-            const float p[3] = {__fmul_rn(z, xn), __fmul_rn(z, yn), z};
-            float P[3];
-            xform(pose.R, pose.t, p, P);
-            const int mx = round_voxel(P[0], prm.inv_vs);
-            const int my = round_voxel(P[1], prm.inv_vs);
-            const int mz = round_voxel(P[2], prm.inv_vs);
-            if (have_prev && mx == pmx && my == pmy && mz == pmz) continue;
+        int k = 0;
+        int pmx = 0x7fffffff, pmy = 0, pmz = 0;
+        BlockCache bc;
+        // Outer loop over the ray's distinct voxels; the inner loop advances through samples
+        // that round to the voxel already visited, so that a warp runs the visit body about
+        // once per distinct voxel rather than once per sample.
+        while (true) {
+            bool found = false;
+            int mx = 0, my = 0, mz = 0;
+            while (k <= 2 * Kb) {
+                const float z = __fadd_rn(D, __fmul_rn((float)(k - Kb), prm.half_vs));
+                ++k;
+                mx = round_voxel(ray_coord(z, dw[0], pose.t[0]), prm.inv_vs);
+                my = round_voxel(ray_coord(z, dw[1], pose.t[1]), prm.inv_vs);
+                mz = round_voxel(ray_coord(z, dw[2], pose.t[2]), prm.inv_vs);
+                if (mx != pmx || my != pmy || mz != pmz) {
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) break;
             pmx = mx;
             pmy = my;
             pmz = mz;
-            have_prev = true;
             const float vc[3] = {__fmul_rn((float)mx, prm.vs), __fmul_rn((float)my, prm.vs),
                                  __fmul_rn((float)mz, prm.vs)};
             const float zv = __fadd_rn(dot_row(pose.RT + 6, vc), pose.tinv[2]);
@@ -111,7 +154,7 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
             if (d > prm.trunc || d < -prm.trunc) continue;
             const float w = d <= prm.eps ? 1.0f : (prm.trunc - d) / (prm.trunc - prm.eps);
             if (!(w > 0.0f)) continue;
-            const long long idx = map.find_or_insert(mx, my, mz, sc.err, &s_new);
+            const long long idx = voxel_index(map, mx, my, mz, bc, sc.err, &s_new);
             if (idx < 0) continue;
             atomicAdd(map.A + idx, make_float4(w * d, w * nwx, w * nwy, w * nwz));
             atomicAdd(map.W + idx, w);

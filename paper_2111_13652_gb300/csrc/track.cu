@@ -46,6 +46,7 @@ __device__ __forceinline__ int exponent_of(double x) { return ((__double2hiint(x
 // elimination.  Back-substitution uses the six pivot reciprocals, formed in parallel.
 __device__ bool solve6_warp(const double* Hb, double damping, long long n_valid, double* xi) {
     const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
     // lane -> entry (i, k) of the augmented upper triangle, 0 <= i <= 5, i <= k <= 6 (k = 6: rhs)
     int ei = 0, ek = 0;
     {
@@ -61,76 +62,76 @@ __device__ bool solve6_warp(const double* Hb, double damping, long long n_valid,
         }
     }
     const bool active = lane < 27;
-    const int lane_of_ii = [&] { int b = 0; for (int r = 0; r < 6; ++r) { if (r == ei) break; b += 7 - r; } return b; }();
     auto idx = [](int i, int k) { return i * 7 - i * (i - 1) / 2 + (k - i); };  // lane of entry (i, k), i <= k
     auto h21 = [](int i, int k) { return i * 6 - i * (i - 1) / 2 + (k - i); };  // index in the 21 terms
-    (void)lane_of_ii;
 
-    double diag[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) diag[k] = Hb[h21(k, k)];
-    double lam = 0.0;
-    if (damping > 0.0) lam = damping * (((diag[0] + diag[1]) + (diag[2] + diag[3])) + (diag[4] + diag[5])) * (1.0 / 6.0);
-    const double maxd = fmax(fmax(fmax(diag[0], diag[1]), fmax(diag[2], diag[3])), fmax(diag[4], diag[5])) + lam;
-    bool pos = n_valid >= 6 && maxd > 0.0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) pos = pos && (diag[k] + lam) > 0.0;
+    // lane-parallel bookkeeping: lane j < 6 owns diagonal entry j
+    const int dj = lane < 6 ? lane : 0;
+    const double myd = lane < 6 ? Hb[h21(dj, dj)] : 0.0;
+    double tr = myd;
+    tr += __shfl_xor_sync(full, tr, 1);
+    tr += __shfl_xor_sync(full, tr, 2);
+    tr += __shfl_xor_sync(full, tr, 4);  // lanes 0..7 hold the trace (lanes 6, 7 contribute 0)
+    tr = __shfl_sync(full, tr, 0);
+    const double lam = damping > 0.0 ? damping * tr * (1.0 / 6.0) : 0.0;
+    const double mydl = myd + lam;
+    double mx = lane < 6 ? mydl : -1.0;
+    mx = fmax(mx, __shfl_xor_sync(full, mx, 1));
+    mx = fmax(mx, __shfl_xor_sync(full, mx, 2));
+    mx = fmax(mx, __shfl_xor_sync(full, mx, 4));
+    const double maxd = __shfl_sync(full, mx, 0);
+    const bool bad_diag = __any_sync(full, lane < 6 && !(mydl > 0.0));
     if (lane < 6) xi[lane] = 0.0;
-    if (!pos) return false;
-    // power-of-two scales s_i (row) and s_k (column; 1 for the rhs column)
-    const double dii = Hb[h21(ei, ei)] + lam;
-    const int ekc = ek < 6 ? ek : ei;
-    const double dkk = Hb[h21(ekc, ekc)] + lam;
-    const double s_i = exp2i(-(exponent_of(dii) >> 1));
-    const double s_k = ek < 6 ? exp2i(-(exponent_of(dkk) >> 1)) : 1.0;
+    if (n_valid < 6 || !(maxd > 0.0) || bad_diag) return false;
+    // power-of-two scales s_j ~ diag_j^-1/2 (exact); lane j < 6 computes its own
+    const double my_s = exp2i(-(exponent_of(lane < 6 ? mydl : 1.0) >> 1));
+    const double s_i = __shfl_sync(full, my_s, ei);
+    // (every lane must execute each shuffle: take it unconditionally, select afterwards)
+    const double s_k_sh = __shfl_sync(full, my_s, ek < 6 ? ek : 0);
+    const double s_k = ek < 6 ? s_k_sh : 1.0;
     double a = 0.0;
-    if (active) a = ek < 6 ? (Hb[h21(ei, ek)] + (ei == ek ? lam : 0.0)) : -Hb[21 + ei];
+    if (active) a = ek < 6 ? (Hb[h21(ei, ek < 6 ? ek : 0)] + (ei == ek ? lam : 0.0)) : -Hb[21 + ei];
     a *= s_i * s_k;
 
     double pn_mine = 1.0;  // lane (j, j) keeps p_j n_j of its step
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         const int jj = idx(j, j);
-        // row-j lanes publish their entry normalised by n_j; the pivot's exponent sets n_j
-        const double p = __shfl_sync(0xffffffffu, a, jj);
+        const double p = __shfl_sync(full, a, jj);
         const double nrm = exp2i(-exponent_of(p > 0.0 ? p : 1.0));
-        const double an = a * nrm;                                   // FP64 #1 (row j uses it)
-        const double pn = __shfl_sync(0xffffffffu, an, jj);
+        const double an = a * nrm;
+        const double pn = __shfl_sync(full, an, jj);
         if (lane == jj) pn_mine = pn;
-        // entry (i, k), i > j: needs a_ji n_j (lane (j, i)) and a_jk (lane (j, k))
         const int src_n = idx(j, ei > j ? ei : j);
         const int src_k = idx(j, ek > j ? ek : j);
-        const double aji_n = __shfl_sync(0xffffffffu, an, src_n);
-        const double ajk = __shfl_sync(0xffffffffu, a, src_k);
-        const double t = pn * a;                                     // FP64 #2
-        const double upd = fma(-aji_n, ajk, t);                      // FP64 #3
+        const double aji_n = __shfl_sync(full, an, src_n);
+        const double ajk = __shfl_sync(full, a, src_k);
+        const double upd = fma(-aji_n, ajk, pn * a);
         if (active && ei > j) a = upd;
     }
-    // pivots p_j (in lanes (j, j)), their running scale sigma_j = prod_{k<j} p_k n_k, the test
-    double pj[6], pnj[6];
+    // pivot test, lane-parallel: lane j < 6 checks p_j > 1e-12 maxd s_j^2 sigma_j with
+    // sigma_j = prod_{k<j} p_k n_k (exclusive prefix product by shuffles)
+    const double pj = __shfl_sync(full, a, idx(dj, dj));
+    const double pnj = __shfl_sync(full, pn_mine, idx(dj, dj));
+    double pre = lane < 6 ? pnj : 1.0;  // inclusive prefix product over lanes 0..5
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        pj[j] = __shfl_sync(0xffffffffu, a, idx(j, j));
-        pnj[j] = __shfl_sync(0xffffffffu, pn_mine, idx(j, j));
+    for (int o = 1; o < 8; o <<= 1) {
+        const double up = __shfl_up_sync(full, pre, o);
+        if (lane >= o) pre *= up;
     }
-    bool ok = true;
-    double sigma = 1.0;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        const double sj = exp2i(-(exponent_of(diag[j] + lam) >> 1));
-        ok = ok && pj[j] > 1e-12 * maxd * (sj * sj) * sigma;
-        sigma *= pnj[j];
-    }
-    if (!ok) return false;
+    double sigma = __shfl_up_sync(full, pre, 1);
+    if (lane == 0) sigma = 1.0;
+    const bool pivot_bad = __any_sync(full, lane < 6 && !(pj > (1e-12 * maxd) * (my_s * my_s) * sigma));
+    if (pivot_bad) return false;
     // back-substitution on the rhs lanes (i, 6): x_k = c_k / p_k, c_i -= a_ik x_k
     const double rcp = 1.0 / (ei == ek ? a : 1.0);        // lanes (k, k): 1 / p_k, all at once
     double c = a;                                            // meaningful in lanes (i, 6)
 #pragma unroll
     for (int k = 5; k >= 0; --k) {
-        const double rk = __shfl_sync(0xffffffffu, rcp, idx(k, k));
-        const double ck = __shfl_sync(0xffffffffu, c, idx(k, 6));
+        const double rk = __shfl_sync(full, rcp, idx(k, k));
+        const double ck = __shfl_sync(full, c, idx(k, 6));
         const double xk = ck * rk;
-        const double aik = __shfl_sync(0xffffffffu, a, idx(ei < k ? ei : k, k));
+        const double aik = __shfl_sync(full, a, idx(ei < k ? ei : k, k));
         if (ek == 6 && ei < k) c = fma(-aik, xk, c);
         if (ek == 6 && ei == k) c = xk;
     }
@@ -169,26 +170,33 @@ __device__ void se3_exp_warp(const double* xi, double* dT) {
     const double A = __shfl_sync(0xffffffffu, coef, 0);
     const double B = __shfl_sync(0xffffffffu, coef, 1);
     const double C = __shfl_sync(0xffffffffu, coef, 2);
-    // row r of [w]x and of w w^T - th2 I, held in registers for every r via selects
+    // every lane evaluates one uniform expression  base + c1 X + c2 Y :
+    //   lanes 0..8  (R entry (r, c)):  I_rc + A [w]x_rc + B ([w]x^2)_rc
+    //   lanes 9..11 (t entry r):       u_r + B (w x u)_r + C (w_r (w.u) - th2 u_r)
     const int r = lane < 9 ? lane / 3 : (lane < 12 ? lane - 9 : 0);
+    const int cc = lane < 9 ? lane - 3 * r : 0;
+    const bool is_t = lane >= 9;
+    const double u0 = xi[3], u1 = xi[4], u2 = xi[5];
     const double wr = r == 0 ? w0 : (r == 1 ? w1 : w2);
-    const double K0 = r == 0 ? 0.0 : (r == 1 ? w2 : -w1);
-    const double K1 = r == 0 ? -w2 : (r == 1 ? 0.0 : w0);
-    const double K2 = r == 0 ? w1 : (r == 1 ? -w0 : 0.0);
-    const double Q0 = wr * w0 - (r == 0 ? th2 : 0.0);
-    const double Q1 = wr * w1 - (r == 1 ? th2 : 0.0);
-    const double Q2 = wr * w2 - (r == 2 ? th2 : 0.0);
-    if (lane < 9) {
-        const int cidx = lane - 3 * r;
-        const double Kc = cidx == 0 ? K0 : (cidx == 1 ? K1 : K2);
-        const double Qc = cidx == 0 ? Q0 : (cidx == 1 ? Q1 : Q2);
-        dT[4 * r + cidx] = ((r == cidx) ? 1.0 : 0.0) + A * Kc + B * Qc;
-    } else if (lane < 12) {
-        const double V0 = ((r == 0) ? 1.0 : 0.0) + B * K0 + C * Q0;
-        const double V1 = ((r == 1) ? 1.0 : 0.0) + B * K1 + C * Q1;
-        const double V2 = ((r == 2) ? 1.0 : 0.0) + B * K2 + C * Q2;
-        dT[4 * r + 3] = (V0 * xi[3] + V1 * xi[4]) + V2 * xi[5];
-    }
+    const double wc = cc == 0 ? w0 : (cc == 1 ? w1 : w2);
+    const double ur = r == 0 ? u0 : (r == 1 ? u1 : u2);
+    // [w]x_rc for r != c: +-w_k with k the remaining index
+    const int kk = 3 - r - cc;
+    const double wk = kk == 0 ? w0 : (kk == 1 ? w1 : w2);
+    const double kx = (r == cc) ? 0.0 : (((cc - r + 3) % 3 == 1) ? -wk : wk);
+    // (w x u)_r = w_{r+1} u_{r+2} - w_{r+2} u_{r+1}
+    const int r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+    const double wa = r1 == 0 ? w0 : (r1 == 1 ? w1 : w2), wb = r2 == 0 ? w0 : (r2 == 1 ? w1 : w2);
+    const double ua = r1 == 0 ? u0 : (r1 == 1 ? u1 : u2), ub = r2 == 0 ? u0 : (r2 == 1 ? u1 : u2);
+    const double wxu = fma(wa, ub, -(wb * ua));
+    const double wu = fma(w0, u0, fma(w1, u1, w2 * u2));
+    const double base = is_t ? ur : ((r == cc) ? 1.0 : 0.0);
+    const double c1 = is_t ? B : A;
+    const double c2 = is_t ? C : B;
+    const double X = is_t ? wxu : kx;
+    const double Y = is_t ? fma(wr, wu, -th2 * ur) : fma(wr, wc, (r == cc) ? -th2 : 0.0);
+    const double v = fma(c2, Y, fma(c1, X, base));
+    if (lane < 12) dT[is_t ? 4 * r + 3 : 4 * r + cc] = v;
     __syncwarp();
 }
 
@@ -270,9 +278,10 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
         if (!depth_ok(D, K.depth_max)) continue;
         const int v = pix / K.width;
         const int u = pix - v * K.width;
-        float p[3], P[3];
-        backproject(K, u, v, D, p);
-        xform(R, t, p, P);
+        float dw[3], P[3];
+        ray_world(K, R, u, v, dw);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) P[i] = ray_coord(D, dw[i], t[i]);
         const int mx = round_voxel(P[0], prm.inv_vs);
         const int my = round_voxel(P[1], prm.inv_vs);
         const int mz = round_voxel(P[2], prm.inv_vs);
