@@ -232,6 +232,49 @@ gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, const gsdf_int
                                           double* T_wc_dev, gsdf_track_stats* stats_dev,
                                           void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many independent scenes (maps of any kind and voxel size, frames of any resolution)
+ * tracked and fused together in persistent launches.  Each Gauss-Newton step of every scene is
+ * one launch over (scene, pixel-tile) items pulled from a device counter.  A scene's 6x6 solve
+ * runs in the block that finishes its last tile while other blocks keep working, so the
+ * per-scene FP64 tail overlaps the other scenes' pixel work.  Results per scene are those of
+ * gsdf_track_step / gsdf_integrate on that scene's handle, up to FP32 summation order.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct gsdf_batch gsdf_batch;
+
+/* Group n handles (all on the current device; not used elsewhere while the batch is in use).
+ * Allocates the batch's descriptor table and counters.  cuda_stream: the stream of every batch
+ * call.  Synchronous. */
+gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda_stream, gsdf_batch** out);
+gsdf_status gsdf_batch_destroy(gsdf_batch* b);
+
+/* Set the frame of every scene: host arrays of n device pointers (depth_dev[s], T_wc_dev[s]) and
+ * n intrinsics; track_stats_dev / integrate_stats_dev: NULL or device arrays of n entries.  The
+ * descriptor table is copied to the device on the batch's stream.  A change of any frame size
+ * rebuilds the tile table (host-synchronous, and uses an autotuned tile size when one is cached for
+ * that set of sizes). */
+gsdf_status gsdf_batch_set_frames(gsdf_batch* b, const float* const* depth_dev, const gsdf_intrinsics* K,
+                                  double* const* T_wc_dev, gsdf_track_stats* track_stats_dev,
+                                  gsdf_integrate_stats* integrate_stats_dev);
+
+/* One Gauss-Newton step of every scene (one persistent launch). */
+gsdf_status gsdf_batch_track_step(gsdf_batch* b);
+
+/* n_iters steps of every scene, recorded once into a CUDA graph and replayed while the tile
+ * table and n_iters stay the same (frames may change between calls through
+ * gsdf_batch_set_frames).  1 <= n_iters <= 1024. */
+gsdf_status gsdf_batch_track(gsdf_batch* b, int32_t n_iters);
+
+/* Fuse every scene's frame at its current pose (prologue, one persistent launch, epilogue). */
+gsdf_status gsdf_batch_integrate(gsdf_batch* b);
+
+/* Choose the tile size (pixels per work item) and the resident blocks per SM of the batched
+ * tracking launch by timing candidates on the current frames: one Gauss-Newton step of every
+ * scene per candidate, run on scratch copies of the poses without statistics, so maps, poses and
+ * statistics are unchanged.  The choice is cached per shape class (the multiset of frame sizes).
+ * Synchronous.  Optional outputs receive the choice. */
+gsdf_status gsdf_batch_autotune(gsdf_batch* b, int32_t* tile_px_out, int32_t* ctas_per_sm_out);
+
 /* Static description of a status code. */
 const char* gsdf_status_string(gsdf_status s);
 

@@ -1,0 +1,517 @@
+// Batched tracking and fusion of many independent scenes in persistent launches.
+//
+// A batch groups existing handles (dense or hashed maps of any voxel size) with one depth frame
+// per scene (any resolution).  The pixels of all scenes are cut into tiles; resident CTAs pull
+// (scene, tile) items from a device counter until none are left.
+//   * Tracking: a tile's 30 normal-equation terms go into its scene's exact fixed-point
+//     accumulators (the same accumulators and arithmetic as the single-scene kernel), and the
+//     CTA that takes a scene's last ticket solves that scene's 6x6 system and updates its pose
+//     while the other CTAs keep working on other scenes, so the serial FP64 tail of every scene
+//     is hidden behind the others' pixel work.  One launch is one Gauss-Newton step of every
+//     scene; gsdf_batch_track records n of them into a CUDA graph that is replayed.
+//   * Fusion: a prologue rounds every scene's pose once, the persistent kernel fuses all
+//     scenes' rays, an epilogue writes the per-scene block totals.
+// The tile size and the number of resident CTAs per SM come from gsdf_batch_autotune, which
+// times the candidates on the batch's own frames (tracking only, on scratch copies of the poses)
+// and caches the choice per shape class (the multiset of image sizes).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "integrate_device.cuh"
+#include "track_device.cuh"
+
+namespace gsdf {
+
+struct SceneDesc {
+    int kind;        // GSDF_GRID_DENSE or GSDF_GRID_HASHED
+    int n_px;        // pixels of the scene's frame
+    int tile_begin;  // first global tile index of the scene
+    int n_tiles;
+    DenseMap dm;
+    HashMap hm;
+    Params prm;
+    Intr K;
+    const float* depth;
+    double* pose;
+    gsdf_track_stats* tstats;
+    gsdf_integrate_stats* istats;
+    unsigned long long* accum;
+    unsigned int* ticket;
+    int* err;
+    unsigned int* n_blocks;
+    PoseF pose32;  // the pose rounded once, written by the fusion prologue
+};
+
+// counters: [0] tracking work, [1] tracking exits, [2] fusion work, [3] fusion exits
+constexpr int kBatchCounters = 4;
+
+__device__ __forceinline__ void batch_exit(unsigned int* work, unsigned int* exited) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned e = atomicAdd(exited, 1u);
+        if (e == gridDim.x - 1) {  // every CTA has taken its last item: reset for the next launch
+            *work = 0u;
+            *exited = 0u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
+batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int total_tiles, int tile_px,
+                   unsigned int* counters) {
+    __shared__ TrackShared sh;
+    __shared__ int s_item;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counters + 0, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total_tiles) break;
+        SceneDesc* d = descs + __ldg(tile_scene + item);
+        load_pose(sh, d->pose);
+        const int lt = item - d->tile_begin;
+        const int p0 = lt * tile_px;
+        const int p1 = min(p0 + tile_px, d->n_px);
+        const Params prm = d->prm;
+        const Intr K = d->K;
+        const float* depth = d->depth;
+        __syncthreads();
+        float acc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+        if (d->kind == GSDF_GRID_DENSE) {
+            const DenseMap m = d->dm;
+            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+                track_pixel(m, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+        } else {
+            const HashMap m = d->hm;
+            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+                track_pixel(m, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+        }
+        block_reduce_terms(sh, acc);
+        if (add_partial_and_ticket(sh, d->accum, d->ticket, lt, (unsigned)d->n_tiles))
+            finish_scene(sh, d->accum, d->ticket, prm, d->pose, d->tstats);
+        __syncthreads();
+    }
+    batch_exit(counters + 0, counters + 1);
+}
+
+// Fusion prologue: round every pose once and clear the per-scene statistics.
+__global__ void batch_prologue_kernel(SceneDesc* descs, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    SceneDesc* d = descs + s;
+    double T[16];
+    for (int i = 0; i < 16; ++i) T[i] = d->pose[i];
+    round_pose(T, d->pose32);
+    if (d->istats) {
+        d->istats->n_rays = 0;
+        d->istats->n_visits = 0;
+        d->istats->n_blocks_new = 0;
+        d->istats->n_blocks_total = 0;
+    }
+}
+
+__global__ void batch_epilogue_kernel(SceneDesc* descs, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    SceneDesc* d = descs + s;
+    if (d->istats) d->istats->n_blocks_total = d->kind == GSDF_GRID_HASHED ? (long long)*d->n_blocks : 0;
+}
+
+constexpr int kBatchIntThreads = 256;
+
+__global__ void __launch_bounds__(kBatchIntThreads)
+batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int total_tiles, int tile_px,
+                       unsigned int* counters) {
+    __shared__ PoseF pose;
+    __shared__ int s_item;
+    __shared__ unsigned int s_rays, s_visits, s_new;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_item = (int)atomicAdd(counters + 2, 1u);
+            s_rays = s_visits = s_new = 0u;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total_tiles) break;
+        SceneDesc* d = descs + __ldg(tile_scene + item);
+        if (threadIdx.x < (int)(sizeof(PoseF) / sizeof(float)))
+            reinterpret_cast<float*>(&pose)[threadIdx.x] = reinterpret_cast<const float*>(&d->pose32)[threadIdx.x];
+        const int lt = item - d->tile_begin;
+        const int p0 = lt * tile_px;
+        const int p1 = min(p0 + tile_px, d->n_px);
+        const Params prm = d->prm;
+        const Intr K = d->K;
+        const float* depth = d->depth;
+        __syncthreads();
+        unsigned int rays = 0, visits = 0;
+        if (d->kind == GSDF_GRID_DENSE) {
+            const DenseMap m = d->dm;
+            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+                integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
+        } else {
+            const HashMap m = d->hm;
+            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+                integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            rays += __shfl_xor_sync(0xffffffffu, rays, o);
+            visits += __shfl_xor_sync(0xffffffffu, visits, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_rays, rays);
+            atomicAdd(&s_visits, visits);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_new) atomicAdd(d->n_blocks, s_new);
+            if (d->istats) {
+                atomicAdd((unsigned long long*)&d->istats->n_rays, (unsigned long long)s_rays);
+                atomicAdd((unsigned long long*)&d->istats->n_visits, (unsigned long long)s_visits);
+                atomicAdd((unsigned long long*)&d->istats->n_blocks_new, (unsigned long long)s_new);
+            }
+        }
+        __syncthreads();
+    }
+    batch_exit(counters + 2, counters + 3);
+}
+
+}  // namespace gsdf
+
+using namespace gsdf;
+
+struct gsdf_batch {
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int num_sms = 0;
+    std::vector<gsdf_handle*> h;
+    SceneDesc* d_desc = nullptr;
+    SceneDesc* h_desc = nullptr;  // pinned staging of the descriptor table
+    cudaEvent_t desc_copied = nullptr;
+    bool desc_pending = false;
+    bool frames_set = false;
+    unsigned int* d_counters = nullptr;
+    double* d_scratch_pose = nullptr;  // autotuning works on copies of the poses
+    int* d_tile_scene = nullptr;
+    int tile_cap = 0;
+    int total_tiles = 0;
+    int tile_px = 2048;
+    int ctas_per_sm = 1;
+    std::vector<int> n_px;  // frame size per scene in the current tile table
+    std::map<std::vector<int>, std::pair<int, int>> tuned;  // shape class -> (tile_px, ctas/SM)
+    cudaGraphExec_t track_exec = nullptr;
+    int g_iters = 0, g_tiles = 0, g_tile_px = 0, g_ctas = 0;
+    const int* g_tile_ptr = nullptr;
+};
+
+namespace {
+
+gsdf_status batch_status(cudaError_t e) {
+    if (e == cudaSuccess) return GSDF_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GSDF_ERR_OOM : GSDF_ERR_CUDA;
+}
+
+bool intr_ok(const gsdf_intrinsics& K) {
+    auto pos = [](float x) { return std::isfinite(x) && x > 0.0f; };
+    return pos(K.fx) && pos(K.fy) && std::isfinite(K.cx) && std::isfinite(K.cy) && K.width > 0 && K.height > 0 &&
+           K.width <= 32768 && K.height <= 32768 && pos(K.depth_max);
+}
+
+void free_batch(gsdf_batch* b) {
+    if (b->track_exec) cudaGraphExecDestroy(b->track_exec);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->desc_copied) cudaEventDestroy(b->desc_copied);
+    cudaFree(b->d_desc);
+    cudaFreeHost(b->h_desc);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_scratch_pose);
+    cudaFree(b->d_tile_scene);
+    delete b;
+}
+
+// (Re)build the tile table for the current frame sizes and tile size; host-synchronous (only when
+// sizes or the tile size change).
+cudaError_t build_tiles(gsdf_batch* b) {
+    std::vector<int> scene_of;
+    int t = 0;
+    for (int s = 0; s < b->n; ++s) {
+        const int nt = (b->n_px[s] + b->tile_px - 1) / b->tile_px;
+        b->h_desc[s].tile_begin = t;
+        b->h_desc[s].n_tiles = nt;
+        for (int k = 0; k < nt; ++k) scene_of.push_back(s);
+        t += nt;
+    }
+    b->total_tiles = t;
+    if (t > b->tile_cap) {
+        cudaFree(b->d_tile_scene);
+        b->d_tile_scene = nullptr;
+        cudaError_t e = cudaMalloc(&b->d_tile_scene, sizeof(int) * (size_t)t);
+        if (e != cudaSuccess) return e;
+        b->tile_cap = t;
+    }
+    return cudaMemcpy(b->d_tile_scene, scene_of.data(), sizeof(int) * (size_t)t, cudaMemcpyHostToDevice);
+}
+
+cudaError_t upload_desc(gsdf_batch* b) {
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(SceneDesc) * (size_t)b->n, cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->desc_copied, b->stream);
+    b->desc_pending = true;
+    return e;
+}
+
+cudaError_t wait_desc(gsdf_batch* b) {
+    if (!b->desc_pending) return cudaSuccess;
+    b->desc_pending = false;
+    return cudaEventSynchronize(b->desc_copied);
+}
+
+cudaError_t launch_batch_track(gsdf_batch* b, cudaStream_t st) {
+    const int grid = std::max(1, std::min(b->total_tiles, b->ctas_per_sm * b->num_sms));
+    batch_track_kernel<<<grid, kTrackThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles, b->tile_px,
+                                                        b->d_counters);
+    return cudaGetLastError();
+}
+
+std::vector<int> shape_class(const gsdf_batch* b) {
+    std::vector<int> k = b->n_px;
+    std::sort(k.begin(), k.end());
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda_stream, gsdf_batch** out) {
+    if (!out || !handles || n < 1 || n > 65536) return GSDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int s = 0; s < n; ++s)
+        if (!handles[s]) return GSDF_ERR_INVALID_ARG;
+    gsdf_batch* b = new (std::nothrow) gsdf_batch();
+    if (!b) return GSDF_ERR_OOM;
+    b->n = n;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->h.assign(handles, handles + n);
+    b->n_px.assign(n, 0);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(SceneDesc) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_desc, sizeof(SceneDesc) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * kBatchCounters);
+    if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * kBatchCounters);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_scratch_pose, sizeof(double) * 16 * (size_t)n);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->desc_copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        gsdf_status st = batch_status(e);
+        free_batch(b);
+        return st;
+    }
+    for (int s = 0; s < n; ++s) {
+        SceneDesc& d = b->h_desc[s];
+        memset(&d, 0, sizeof(d));
+        const gsdf_handle* hh = handles[s];
+        d.kind = hh->hashed ? GSDF_GRID_HASHED : GSDF_GRID_DENSE;
+        d.dm = hh->dm;
+        d.hm = hh->hm;
+        d.prm = hh->prm;
+        d.accum = hh->sc.accum;
+        d.ticket = hh->sc.counter;
+        d.err = hh->sc.err;
+        d.n_blocks = hh->sc.n_blocks;
+    }
+    *out = b;
+    return GSDF_OK;
+}
+
+gsdf_status gsdf_batch_destroy(gsdf_batch* b) {
+    if (!b) return GSDF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return batch_status(e);
+}
+
+gsdf_status gsdf_batch_set_frames(gsdf_batch* b, const float* const* depth_dev, const gsdf_intrinsics* K,
+                                  double* const* T_wc_dev, gsdf_track_stats* track_stats_dev,
+                                  gsdf_integrate_stats* integrate_stats_dev) {
+    if (!b || !depth_dev || !K || !T_wc_dev) return GSDF_ERR_INVALID_ARG;
+    for (int s = 0; s < b->n; ++s)
+        if (!depth_dev[s] || !T_wc_dev[s] || !intr_ok(K[s])) return GSDF_ERR_INVALID_ARG;
+    cudaError_t e = wait_desc(b);  // the pinned table may still be in flight from the last call
+    if (e != cudaSuccess) return batch_status(e);
+    bool resized = !b->frames_set;
+    for (int s = 0; s < b->n; ++s) {
+        SceneDesc& d = b->h_desc[s];
+        const int npx = K[s].width * K[s].height;
+        resized = resized || npx != b->n_px[s];
+        b->n_px[s] = npx;
+        d.n_px = npx;
+        d.K.fx = K[s].fx;
+        d.K.fy = K[s].fy;
+        d.K.cx = K[s].cx;
+        d.K.cy = K[s].cy;
+        d.K.width = K[s].width;
+        d.K.height = K[s].height;
+        d.K.depth_max = K[s].depth_max;
+        d.K.ifx = (float)(1.0 / (double)K[s].fx);
+        d.K.ify = (float)(1.0 / (double)K[s].fy);
+        d.depth = depth_dev[s];
+        d.pose = T_wc_dev[s];
+        d.tstats = track_stats_dev ? track_stats_dev + s : nullptr;
+        d.istats = integrate_stats_dev ? integrate_stats_dev + s : nullptr;
+    }
+    if (resized) {
+        auto it = b->tuned.find(shape_class(b));
+        if (it != b->tuned.end()) {
+            b->tile_px = it->second.first;
+            b->ctas_per_sm = it->second.second;
+        }
+        e = build_tiles(b);
+        if (e != cudaSuccess) return batch_status(e);
+    }
+    b->frames_set = true;
+    return batch_status(upload_desc(b));
+}
+
+gsdf_status gsdf_batch_track_step(gsdf_batch* b) {
+    if (!b || !b->frames_set) return GSDF_ERR_INVALID_ARG;
+    return batch_status(launch_batch_track(b, b->stream));
+}
+
+gsdf_status gsdf_batch_track(gsdf_batch* b, int32_t n_iters) {
+    if (!b || !b->frames_set || n_iters < 1 || n_iters > 1024) return GSDF_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(b->stream, &cs);
+    if (e != cudaSuccess) return batch_status(e);
+    if (cs != cudaStreamCaptureStatusNone) {
+        for (int it = 0; it < n_iters && e == cudaSuccess; ++it) e = launch_batch_track(b, b->stream);
+        return batch_status(e);
+    }
+    const bool same = b->track_exec && b->g_iters == n_iters && b->g_tiles == b->total_tiles &&
+                      b->g_tile_px == b->tile_px && b->g_ctas == b->ctas_per_sm && b->g_tile_ptr == b->d_tile_scene;
+    if (!same) {
+        if (b->track_exec) {
+            cudaGraphExecDestroy(b->track_exec);
+            b->track_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return batch_status(e);
+        cudaError_t le = cudaSuccess;
+        for (int it = 0; it < n_iters && le == cudaSuccess; ++it) le = launch_batch_track(b, b->capture_stream);
+        e = cudaStreamEndCapture(b->capture_stream, &graph);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->track_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->track_exec = nullptr;
+            return batch_status(e);
+        }
+        b->g_iters = n_iters;
+        b->g_tiles = b->total_tiles;
+        b->g_tile_px = b->tile_px;
+        b->g_ctas = b->ctas_per_sm;
+        b->g_tile_ptr = b->d_tile_scene;
+    }
+    return batch_status(cudaGraphLaunch(b->track_exec, b->stream));
+}
+
+gsdf_status gsdf_batch_integrate(gsdf_batch* b) {
+    if (!b || !b->frames_set) return GSDF_ERR_INVALID_ARG;
+    const int pro = (b->n + 127) / 128;
+    batch_prologue_kernel<<<pro, 128, 0, b->stream>>>(b->d_desc, b->n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return batch_status(e);
+    const int grid = std::max(1, std::min(b->total_tiles, 6 * b->num_sms));
+    batch_integrate_kernel<<<grid, kBatchIntThreads, 0, b->stream>>>(b->d_desc, b->d_tile_scene, b->total_tiles,
+                                                                     b->tile_px, b->d_counters);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return batch_status(e);
+    batch_epilogue_kernel<<<pro, 128, 0, b->stream>>>(b->d_desc, b->n);
+    return batch_status(cudaGetLastError());
+}
+
+gsdf_status gsdf_batch_autotune(gsdf_batch* b, int32_t* tile_px_out, int32_t* ctas_per_sm_out) {
+    if (!b || !b->frames_set) return GSDF_ERR_INVALID_ARG;
+    const std::vector<int> key = shape_class(b);
+    auto it = b->tuned.find(key);
+    if (it == b->tuned.end()) {
+        cudaError_t e = wait_desc(b);
+        if (e != cudaSuccess) return batch_status(e);
+        // time one Gauss-Newton step of every scene per candidate, on scratch copies of the poses
+        // and without statistics, so that the maps, poses and statistics are left untouched
+        std::vector<SceneDesc> saved(b->h_desc, b->h_desc + b->n);
+        for (int s = 0; s < b->n; ++s) {
+            e = cudaMemcpyAsync(b->d_scratch_pose + 16 * s, saved[s].pose, sizeof(double) * 16,
+                                cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) return batch_status(e);
+            b->h_desc[s].pose = b->d_scratch_pose + 16 * s;
+            b->h_desc[s].tstats = nullptr;
+        }
+        const int tiles[] = {512, 1024, 2048, 4096, 8192};
+        const int ctas[] = {1, 2};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_tile = b->tile_px, best_ctas = b->ctas_per_sm;
+        for (int tp : tiles) {
+            b->tile_px = tp;
+            e = build_tiles(b);
+            if (e == cudaSuccess) e = upload_desc(b);
+            if (e == cudaSuccess) e = wait_desc(b);
+            for (int c : ctas) {
+                if (e != cudaSuccess) break;
+                b->ctas_per_sm = c;
+                e = launch_batch_track(b, b->stream);  // warm-up
+                float ms_sum = 0.0f;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    cudaEventRecord(e0, b->stream);
+                    e = launch_batch_track(b, b->stream);
+                    cudaEventRecord(e1, b->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms_sum += ms;
+                }
+                if (e == cudaSuccess && ms_sum < best) {
+                    best = ms_sum;
+                    best_tile = tp;
+                    best_ctas = c;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (int s = 0; s < b->n; ++s) b->h_desc[s] = saved[s];
+        b->tile_px = best_tile;
+        b->ctas_per_sm = best_ctas;
+        cudaError_t e2 = build_tiles(b);
+        if (e2 == cudaSuccess) e2 = upload_desc(b);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return batch_status(e);
+        b->tuned[key] = {best_tile, best_ctas};
+    } else {
+        if (it->second.first != b->tile_px || it->second.second != b->ctas_per_sm) {
+            cudaError_t e = wait_desc(b);
+            b->tile_px = it->second.first;
+            b->ctas_per_sm = it->second.second;
+            if (e == cudaSuccess) e = build_tiles(b);
+            if (e == cudaSuccess) e = upload_desc(b);
+            if (e != cudaSuccess) return batch_status(e);
+        }
+    }
+    if (tile_px_out) *tile_px_out = b->tile_px;
+    if (ctas_per_sm_out) *ctas_per_sm_out = b->ctas_per_sm;
+    return GSDF_OK;
+}
+
+}  // extern "C"

@@ -9,26 +9,6 @@
 
 using namespace gsdf;
 
-struct gsdf_handle {
-    gsdf_config cfg;
-    cudaStream_t stream;
-    int device;
-    int num_sms;
-    bool hashed;
-    long long n_voxels;  // payload entries (dense box or slots * 512)
-    DenseMap dm;
-    HashMap hm;
-    Params prm;
-    Scratch sc;
-    // cached CUDA graph of gsdf_track's launches, keyed by its arguments
-    cudaStream_t capture_stream;
-    cudaGraphExec_t track_exec;
-    const float* g_depth;
-    double* g_pose;
-    gsdf_track_stats* g_stats;
-    int g_iters;
-    gsdf_intrinsics g_K;
-};
 
 namespace {
 

@@ -243,3 +243,25 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_sl
 cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const gsdf_voxel* in_dev, long long n,
                         int* err, unsigned int* n_blocks, cudaStream_t st, int num_sms);
 }  // namespace gsdf
+
+// A map handle (the C ABI's opaque gsdf_handle).
+struct gsdf_handle {
+    gsdf_config cfg;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    bool hashed;
+    long long n_voxels;  // payload entries (dense box or slots * 512)
+    gsdf::DenseMap dm;
+    gsdf::HashMap hm;
+    gsdf::Params prm;
+    gsdf::Scratch sc;
+    // cached CUDA graph of gsdf_track's launches, keyed by its arguments
+    cudaStream_t capture_stream;
+    cudaGraphExec_t track_exec;
+    const float* g_depth;
+    double* g_pose;
+    gsdf_track_stats* g_stats;
+    int g_iters;
+    gsdf_intrinsics g_K;
+};

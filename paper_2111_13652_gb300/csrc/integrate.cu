@@ -11,86 +11,9 @@
 // average of Eq. (sdf_update) up to summation order.  The loop runs over distinct voxels, not
 // samples, so the lanes of a warp stay converged on the expensive visit body, and the last block
 // looked up is cached per ray.
-#include "gsdf_internal.cuh"
+#include "integrate_device.cuh"
 
 namespace gsdf {
-
-constexpr int kIntThreads = 256;
-
-// Normal of pixel (u, v) from its 4-neighbours (FP32 index path).  Returns false if the pixel
-// is rejected: image border, invalid neighbour, depth jump > T, zero cross product, or an angle
-// to the viewing ray of 75 degrees or more (cos < cos_max).
-__device__ __forceinline__ bool pixel_normal(const float* __restrict__ depth, const Intr& K,
-                                             const Params& prm, int u, int v, float D, float n[3]) {
-    if (u < 1 || u >= K.width - 1 || v < 1 || v >= K.height - 1) return false;
-    const size_t row = (size_t)v * K.width;
-    const float Dl = __ldg(depth + row + u - 1), Dr = __ldg(depth + row + u + 1);
-    const float Du = __ldg(depth + row - K.width + u), Dd = __ldg(depth + row + K.width + u);
-    const float nb[4] = {Dl, Dr, Du, Dd};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (!depth_ok(nb[i], K.depth_max)) return false;
-        const float diff = __fsub_rn(nb[i], D);
-        if (diff > prm.trunc || diff < -prm.trunc) return false;
-    }
-    float pl[3], pr[3], pu[3], pd[3], p[3];
-    backproject(K, u - 1, v, Dl, pl);
-    backproject(K, u + 1, v, Dr, pr);
-    backproject(K, u, v - 1, Du, pu);
-    backproject(K, u, v + 1, Dd, pd);
-    backproject(K, u, v, D, p);
-    const float a[3] = {__fsub_rn(pr[0], pl[0]), __fsub_rn(pr[1], pl[1]), __fsub_rn(pr[2], pl[2])};
-    const float b[3] = {__fsub_rn(pd[0], pu[0]), __fsub_rn(pd[1], pu[1]), __fsub_rn(pd[2], pu[2])};
-    n[0] = __fsub_rn(__fmul_rn(a[1], b[2]), __fmul_rn(a[2], b[1]));
-    n[1] = __fsub_rn(__fmul_rn(a[2], b[0]), __fmul_rn(a[0], b[2]));
-    n[2] = __fsub_rn(__fmul_rn(a[0], b[1]), __fmul_rn(a[1], b[0]));
-    const float nn = dot3_rn(n, n);
-    if (!(nn > 0.0f)) return false;
-    const float s = __fsqrt_rn(nn);
-    n[0] = __fdiv_rn(n[0], s);
-    n[1] = __fdiv_rn(n[1], s);
-    n[2] = __fdiv_rn(n[2], s);
-    float dp = dot3_rn(n, p);
-    if (dp < 0.0f) {
-        n[0] = -n[0];
-        n[1] = -n[1];
-        n[2] = -n[2];
-        dp = -dp;
-    }
-    const float c = __fdiv_rn(dp, __fsqrt_rn(dot3_rn(p, p)));
-    return c >= prm.cos_max;
-}
-
-// Per-ray cache of the last block looked up: consecutive voxels of a ray mostly share a block.
-struct BlockCache {
-    int bx = 0x7fffffff, by = 0, bz = 0;
-    long long base = -1;  // payload index of local voxel 0, or -1 when the block is unusable
-};
-
-template <class Map>
-__device__ __forceinline__ long long voxel_index(const Map& map, int mx, int my, int mz, BlockCache& bc,
-                                                 int* err, unsigned int* n_new);
-
-template <>
-__device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, int mx, int my, int mz, BlockCache& bc,
-                                                          int* err, unsigned int* n_new) {
-    const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
-    if (bx != bc.bx || by != bc.by || bz != bc.bz) {
-        const long long idx = map.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
-        bc.bx = bx;
-        bc.by = by;
-        bc.bz = bz;
-        bc.base = idx;
-    }
-    if (bc.base < 0) return -1;
-    return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
-}
-
-template <>
-__device__ __forceinline__ long long voxel_index<DenseMap>(const DenseMap& map, int mx, int my, int mz, BlockCache&,
-                                                           int*, unsigned int*) {
-    return map.find(mx, my, mz);
-}
 
 template <class Map>
 __global__ void __launch_bounds__(kIntThreads)
@@ -108,59 +31,8 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
 
     const int n_px = K.width * K.height;
     unsigned int my_rays = 0, my_visits = 0;
-    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x) {
-        const float D = __ldg(depth + pix);
-        if (!depth_ok(D, K.depth_max)) continue;
-        const int v = pix / K.width;
-        const int u = pix - v * K.width;
-        float n[3];
-        if (!pixel_normal(depth, K, prm, u, v, D, n)) continue;
-        ++my_rays;
-        // world normal R n (value path)
-        const float nwx = pose.R[0] * n[0] + pose.R[1] * n[1] + pose.R[2] * n[2];
-        const float nwy = pose.R[3] * n[0] + pose.R[4] * n[1] + pose.R[5] * n[2];
-        const float nwz = pose.R[6] * n[0] + pose.R[7] * n[1] + pose.R[8] * n[2];
-        float dw[3];
-        ray_world(K, pose.R, u, v, dw);
-        const int Kb = prm.band_half;
-        int k = 0;
-        int pmx = 0x7fffffff, pmy = 0, pmz = 0;
-        BlockCache bc;
-        // Outer loop over the ray's distinct voxels; the inner loop advances through samples
-        // that round to the voxel already visited, so that a warp runs the visit body about
-        // once per distinct voxel rather than once per sample.
-        while (true) {
-            bool found = false;
-            int mx = 0, my = 0, mz = 0;
-            while (k <= 2 * Kb) {
-                const float z = __fadd_rn(D, __fmul_rn((float)(k - Kb), prm.half_vs));
-                ++k;
-                mx = round_voxel(ray_coord(z, dw[0], pose.t[0]), prm.inv_vs);
-                my = round_voxel(ray_coord(z, dw[1], pose.t[1]), prm.inv_vs);
-                mz = round_voxel(ray_coord(z, dw[2], pose.t[2]), prm.inv_vs);
-                if (mx != pmx || my != pmy || mz != pmz) {
-                    found = true;
-                    break;
-                }
-            }
-            if (!found) break;
-            pmx = mx;
-            pmy = my;
-            pmz = mz;
-            const float vc[3] = {__fmul_rn((float)mx, prm.vs), __fmul_rn((float)my, prm.vs),
-                                 __fmul_rn((float)mz, prm.vs)};
-            const float zv = __fadd_rn(dot_row(pose.RT + 6, vc), pose.tinv[2]);
-            const float d = __fsub_rn(zv, D);
-            if (d > prm.trunc || d < -prm.trunc) continue;
-            const float w = d <= prm.eps ? 1.0f : (prm.trunc - d) / (prm.trunc - prm.eps);
-            if (!(w > 0.0f)) continue;
-            const long long idx = voxel_index(map, mx, my, mz, bc, sc.err, &s_new);
-            if (idx < 0) continue;
-            atomicAdd(map.A + idx, make_float4(w * d, w * nwx, w * nwy, w * nwz));
-            atomicAdd(map.W + idx, w);
-            ++my_visits;
-        }
-    }
+    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x)
+        integrate_ray(map, depth, K, prm, pose, pix, sc.err, &s_new, my_rays, my_visits);
     // block-aggregated statistics
     for (int o = 16; o > 0; o >>= 1) {
         my_rays += __shfl_xor_sync(0xffffffffu, my_rays, o);

@@ -73,6 +73,14 @@ _SIGS = {
     "gsdf_num_blocks": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "gsdf_sync": (C.c_int, [C.c_void_p]),
     "gsdf_status_string": (C.c_char_p, [C.c_int]),
+    "gsdf_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, _P(C.c_void_p)]),
+    "gsdf_batch_destroy": (C.c_int, [C.c_void_p]),
+    "gsdf_batch_set_frames": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), _P(gsdf_intrinsics),
+                                        C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p]),
+    "gsdf_batch_track_step": (C.c_int, [C.c_void_p]),
+    "gsdf_batch_track": (C.c_int, [C.c_void_p, C.c_int32]),
+    "gsdf_batch_integrate": (C.c_int, [C.c_void_p]),
+    "gsdf_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int32), _P(C.c_int32)]),
     "gsdf_track_step_dense_noalloc": (C.c_int, [C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p,
                                                 _P(C.c_int32), _P(C.c_int32), C.c_float, C.c_float, C.c_double,
                                                 C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -295,3 +303,54 @@ class Map:
 
     def load(self, vox: np.ndarray):
         _check(gsdf_load_voxels(self.h, vox), "gsdf_load_voxels")
+
+
+class Batch:
+    """Many scenes (Map objects) tracked and fused together in persistent launches."""
+
+    def __init__(self, maps, stream=None):
+        import torch
+
+        self.torch = torch
+        self.maps = list(maps)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (C.c_void_p * len(self.maps))(*[m.h for m in self.maps])
+        h = C.c_void_p()
+        _check(load_library().gsdf_batch_create(arr, len(self.maps), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "gsdf_batch_create")
+        self.b = h.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            load_library().gsdf_batch_destroy(C.c_void_p(self.b))
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_frames(self, depths, Ks, poses, track_stats=None, integrate_stats=None):
+        n = len(self.maps)
+        d = (C.c_void_p * n)(*[x.data_ptr() for x in depths])
+        p = (C.c_void_p * n)(*[x.data_ptr() for x in poses])
+        k = (gsdf_intrinsics * n)(*Ks)
+        _check(load_library().gsdf_batch_set_frames(
+            C.c_void_p(self.b), d, k, p,
+            C.c_void_p(track_stats.data_ptr() if track_stats is not None else None),
+            C.c_void_p(integrate_stats.data_ptr() if integrate_stats is not None else None)), "gsdf_batch_set_frames")
+
+    def track_step(self):
+        _check(load_library().gsdf_batch_track_step(C.c_void_p(self.b)), "gsdf_batch_track_step")
+
+    def track(self, n_iters: int):
+        _check(load_library().gsdf_batch_track(C.c_void_p(self.b), n_iters), "gsdf_batch_track")
+
+    def integrate(self):
+        _check(load_library().gsdf_batch_integrate(C.c_void_p(self.b)), "gsdf_batch_integrate")
+
+    def autotune(self):
+        t, c = C.c_int32(), C.c_int32()
+        _check(load_library().gsdf_batch_autotune(C.c_void_p(self.b), C.byref(t), C.byref(c)), "gsdf_batch_autotune")
+        return t.value, c.value

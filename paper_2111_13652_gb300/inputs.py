@@ -393,3 +393,77 @@ def room_sequence(seed: int = 2, n_frames: int = 100, cam: Camera = KINECT_640, 
         d = render_depth(scene, cam, T)
         depths[f] = add_depth_noise(d, rng) if noise else d
     return RoomSequence(cam, scene, poses, depths, voxel_size, 5 * voxel_size)
+
+
+# --------------------------------------------------------------------------------------------
+# the batch workload: many independent scenes of uneven sizes
+# --------------------------------------------------------------------------------------------
+
+RESOLUTIONS = [(160, 120), (320, 240), (480, 360), (640, 480)]
+
+
+def scaled_camera(width, height) -> Camera:
+    """Kinect-like intrinsics scaled to the resolution (f = 525 at 640 px)."""
+    f = 525.0 * width / 640.0
+    return Camera(f, f, width / 2.0 - 0.5, height / 2.0 - 0.5, width, height, 3.5)
+
+
+@dataclasses.dataclass
+class BatchScene:
+    index: int
+    cam: Camera
+    voxel_size: float
+    dense_dims: tuple | None  # None: hashed map
+    dense_origin: tuple | None
+    hash_slots: int
+    damping: float
+    poses: list
+    depths: np.ndarray  # (F, H, W) FP32
+
+
+def sphere_orbit_poses(n_frames: int, seed: int, radius=0.5, deg_per_frame=1.5) -> list:
+    """Camera on a tilted circle around the origin, looking at it."""
+    rng = np.random.default_rng(seed)
+    tilt = rng.uniform(-0.5, 0.5)
+    phase = rng.uniform(0, 2 * math.pi)
+    poses = []
+    for f in range(n_frames):
+        a = phase + math.radians(deg_per_frame) * f
+        c = radius * np.array([math.cos(a) * math.cos(tilt), math.sin(a) * math.cos(tilt), math.sin(tilt)])
+        poses.append(look_at(c, np.zeros(3), roll=0.3 * math.sin(a)))
+    return poses
+
+
+def batch_scene(index: int, n_frames: int, seed: int = 5) -> BatchScene:
+    """Scene `index` of the batch workload: resolution and voxel size cycle with index mod 4;
+    index mod 4 == 0 is a dense 64^3 grid around a sphere, the others hashed rooms."""
+    kind = index % 4
+    w, h = RESOLUTIONS[kind]
+    cam = scaled_camera(w, h)
+    vs = 0.01 * (1 + kind)
+    rng = np.random.default_rng(seed * 1000 + index)
+    if kind == 0:
+        scene = SphereScene(np.zeros(3), float(rng.uniform(0.18, 0.24)))
+        poses = sphere_orbit_poses(n_frames, seed * 1000 + index, radius=float(rng.uniform(0.45, 0.6)))
+        dims, origin, slots, damping = (64, 64, 64), (-32, -32, -32), 1, 1e-4
+    else:
+        scene = make_room(seed * 1000 + index)
+        poses = room_trajectory(scene, n_frames, seed * 1000 + index)
+        dims, origin, damping = None, None, 0.0
+        slots = 1 << 13  # 2e6 voxels of capacity at a load factor below 1/2
+    depths = np.empty((n_frames, h, w), np.float32)
+    for f, T in enumerate(poses):
+        depths[f] = add_depth_noise(render_depth(scene, cam, T), rng)
+    return BatchScene(index, cam, vs, dims, origin, slots, damping, poses, depths)
+
+
+def batch_scenes(n_scenes: int, n_frames: int, seed: int = 5, processes: int = 1) -> list:
+    """All scenes of the batch workload; `processes` > 1 ray-casts them in a spawned pool."""
+    if processes > 1:
+        import concurrent.futures as cf
+        import functools
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(functools.partial(batch_scene, n_frames=n_frames, seed=seed), range(n_scenes)))
+    return [batch_scene(i, n_frames, seed) for i in range(n_scenes)]
