@@ -308,6 +308,8 @@ def gpu_arm(args):
         forms = {}
         if batch_scenes is not None:
             forms["batched_64_scenes"] = batch_form(G, torch, dev, stream, batch_scenes)
+        if not args.no_fp16_form:
+            forms["fp16_payload_4mm"] = fp16_form(G, torch, dev, stream, seq)
     clocks = clk.summary()
     clocks["window"] = "whole GPU run (warm-up, timed steps, e2e repeat); 100 ms sampling"
 
@@ -480,6 +482,67 @@ def batch_form(G, torch, dev, stream, scenes):
     }
 
 
+FP16_WARMUP = 3
+FP16_STEPS = 12
+FP16_VOXEL = 0.004
+FP16_SLOTS = 1 << 17
+
+
+def fp16_form(G, torch, dev, stream, seq):
+    """The room at 4 mm voxels (T = 2 cm): the per-frame loop with the FP32 payload and with the
+    FP16 payload (per-block scale), same frames, same timing rules."""
+    K = G.intrinsics(seq.cam)
+    H, W = seq.cam.height, seq.cam.width
+    depths = torch.from_numpy(seq.depths[:1 + FP16_WARMUP + FP16_STEPS]).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for mode in ("fp32", "fp16"):
+        m = G.Map(G.make_config(FP16_VOXEL, hash_slots=FP16_SLOTS, fp16=(mode == "fp16"),
+                                max_touched_blocks=FP16_SLOTS // 2), stream)
+        pose = torch.from_numpy(np.ascontiguousarray(seq.poses[0])).to(dev)
+        dbuf = torch.empty((H, W), dtype=torch.float32, device=dev)
+        dbuf.copy_(depths[0])
+        m.integrate(dbuf, K, pose)
+        ev = []
+        for f in range(1, 1 + FP16_WARMUP + FP16_STEPS):
+            timed = f > FP16_WARMUP
+            if timed:
+                flush.fill_(f & 0xFF)
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+            dbuf.copy_(depths[f], non_blocking=True)
+            m.track(dbuf, K, pose, GN_ITERS)
+            if timed:
+                e[1].record(stream)
+            m.integrate(dbuf, K, pose)
+            if timed:
+                e[2].record(stream)
+                ev.append(e)
+        torch.cuda.synchronize(dev)
+        st = G.gsdf_sync(m.h)
+        T = pose.cpu().numpy()
+        gt = seq.poses[FP16_WARMUP + FP16_STEPS]
+        out[mode] = {
+            "ms_per_frame": float(np.mean([e[0].elapsed_time(e[2]) for e in ev])),
+            "track_us_per_step": 1e3 * float(np.mean([e[0].elapsed_time(e[1]) for e in ev])) / GN_ITERS,
+            "integrate_us": 1e3 * float(np.mean([e[1].elapsed_time(e[2]) for e in ev])),
+            "voxels": 0, "blocks": m.num_blocks(),
+            "payload_bytes_per_voxel": 12 if mode == "fp16" else 20,
+            "pose_error_m": float(np.linalg.norm(T[:3, 3] - gt[:3, 3])), "status": int(st),
+        }
+        out[mode]["voxels"] = int(len(m.extract()))
+        out[mode]["final_pose"] = T
+        m.close()
+    diff = float(np.abs(out["fp16"].pop("final_pose") - out["fp32"].pop("final_pose")).max())
+    return {
+        "workload": f"hashed room at 4 mm voxels (T = 2 cm), 640x480, {GN_ITERS} GN steps + fusion per frame, "
+                    f"{FP16_WARMUP} warm-up frames, {FP16_STEPS} timed",
+        "fp32": out["fp32"], "fp16": out["fp16"],
+        "max_pose_diff_fp16_vs_fp32": diff,
+        "speedup_fp16_vs_fp32": out["fp32"]["ms_per_frame"] / out["fp16"]["ms_per_frame"],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,6 +551,7 @@ def main():
     ap.add_argument("--impl", default="gsdf", choices=["gsdf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-form", action="store_true")
+    ap.add_argument("--no-fp16-form", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -56,6 +56,7 @@ typedef enum {
 } gsdf_status;
 
 enum { GSDF_GRID_DENSE = 0, GSDF_GRID_HASHED = 1 };
+enum { GSDF_PAYLOAD_F32 = 0, GSDF_PAYLOAD_F16 = 1 };
 
 /* Pinhole intrinsics (Sec. 5.3 uses 640x480 TUM frames, depth cut off at 3.5 m). */
 typedef struct {
@@ -78,7 +79,16 @@ typedef struct {
  *                  0 = plain Gauss-Newton (Sec. 5.1)
  *   hash_slots     number of hash slots (power of two); each slot owns one 8^3 block payload
  *                  (10 KB); hashed only
- *   max_probe      linear-probe limit of the hash table (> 0); hashed only */
+ *   max_probe      linear-probe limit of the hash table (> 0); hashed only
+ *   payload        voxel storage.  GSDF_PAYLOAD_F32: (W psi, g) and W in FP32, 20 bytes per voxel,
+ *                  fused by atomic sums.  GSDF_PAYLOAD_F16 (hashed only): psi / sigma_b and
+ *                  gbar = g / W as four FP16 values with one FP32 scale sigma_b per block (the
+ *                  largest |psi| the block has held), and W in FP32: 12 bytes per voxel.  Per-pixel
+ *                  arithmetic stays FP32; a frame is fused into FP32 accumulators of the touched
+ *                  blocks, then folded into them and re-encoded with round-to-nearest, so psi
+ *                  carries an error of at most 2^-11 sigma_b per frame and ghat about 5e-4.
+ *   max_touched_blocks  FP16 payload only: capacity of the per-frame accumulators, in blocks;
+ *                  a frame touching more blocks is fused partially and reports GSDF_ERR_CAPACITY */
 typedef struct {
     int32_t grid_kind;
     int32_t dense_dims[3];
@@ -91,7 +101,9 @@ typedef struct {
     double damping;
     int64_t hash_slots;
     int32_t max_probe;
-    int32_t reserved;
+    int32_t payload;             /* GSDF_PAYLOAD_F32 or GSDF_PAYLOAD_F16 (hashed maps only) */
+    int32_t max_touched_blocks;  /* FP16 payload: blocks a single frame may update (>= 1) */
+    int32_t pad;
 } gsdf_config;
 
 /* Written by gsdf_track_step into device memory.  H is the upper triangle (row-major, 21
@@ -244,7 +256,7 @@ typedef struct gsdf_batch gsdf_batch;
 
 /* Group n handles (all on the current device; not used elsewhere while the batch is in use).
  * Allocates the batch's descriptor table and counters.  cuda_stream: the stream of every batch
- * call.  Synchronous. */
+ * call.  FP16-payload handles are not accepted (GSDF_ERR_INVALID_ARG).  Synchronous. */
 gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda_stream, gsdf_batch** out);
 gsdf_status gsdf_batch_destroy(gsdf_batch* b);
 

@@ -93,6 +93,7 @@ __global__ void chunk_write_kernel(const unsigned long long* __restrict__ sorted
                                    const long long* __restrict__ base, const long long* __restrict__ offsets,
                                    const float4* __restrict__ A, const float* __restrict__ W,
                                    long long dense_voxels, int dx, int dy, int ox, int oy, int oz,
+                                   const ushort4* __restrict__ H16, const float* __restrict__ scale16,
                                    gsdf_voxel* out) {
     __shared__ unsigned int warp_off[kBlockVoxels / 32];
     for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
@@ -128,12 +129,20 @@ __global__ void chunk_write_kernel(const unsigned long long* __restrict__ sorted
                 o.m[1] = oy + (int)y;
                 o.m[2] = oz + (int)z;
             }
-            const float4 a = A[i];
             const float w = W[i];
-            o.psi = a.x / w;
-            o.g[0] = a.y;
-            o.g[1] = a.z;
-            o.g[2] = a.w;
+            if (H16) {  // FP16 payload: psi = sigma_b * psi~, g = W * gbar
+                const ushort4 h = H16[i];
+                o.psi = __half2float(__ushort_as_half(h.x)) * scale16[i >> 9];
+                o.g[0] = __half2float(__ushort_as_half(h.y)) * w;
+                o.g[1] = __half2float(__ushort_as_half(h.z)) * w;
+                o.g[2] = __half2float(__ushort_as_half(h.w)) * w;
+            } else {
+                const float4 a = A[i];
+                o.psi = a.x / w;
+                o.g[0] = a.y;
+                o.g[1] = a.z;
+                o.g[2] = a.w;
+            }
             o.w = w;
             out[pos] = o;
         }
@@ -151,6 +160,25 @@ __global__ void load_kernel_hashed(HashMap hm, const gsdf_voxel* __restrict__ in
         if (idx < 0) continue;
         hm.A[idx] = make_float4(v.w * v.psi, v.g[0], v.g[1], v.g[2]);
         hm.W[idx] = v.w;
+    }
+}
+
+// FP16 maps: blocks receive the scale sigma_b = T, voxels (psi / T, g / W) rounded to nearest
+__global__ void load_kernel_hashed16(HashMap16 hm, const gsdf_voxel* __restrict__ in, long long n, float trunc,
+                                     int* err, unsigned int* n_new) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const gsdf_voxel v = in[i];
+        const long long idx = hm.base.find_or_insert(v.m[0], v.m[1], v.m[2], err, n_new);
+        if (idx < 0) continue;
+        ushort4 o;
+        o.x = __half_as_ushort(__float2half_rn(v.psi / trunc));
+        o.y = __half_as_ushort(__float2half_rn(v.g[0] / v.w));
+        o.z = __half_as_ushort(__float2half_rn(v.g[1] / v.w));
+        o.w = __half_as_ushort(__float2half_rn(v.g[2] / v.w));
+        hm.H[idx] = o;
+        hm.W[idx] = v.w;
+        hm.scale[idx >> 9] = trunc;
     }
 }
 
@@ -197,8 +225,8 @@ struct DevBuf {
         if (e_ != cudaSuccess) return e_;     \
     } while (0)
 
-cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_slots, cudaStream_t st,
-                           int num_sms, gsdf_voxel** out_dev, long long* n_out) {
+cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
+                           cudaStream_t st, int num_sms, gsdf_voxel** out_dev, long long* n_out) {
     *out_dev = nullptr;
     *n_out = 0;
     const unsigned grid = (unsigned)(num_sms * 8);
@@ -238,7 +266,7 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_sl
     GSDF_CK(counts.alloc((size_t)n_chunks));
     GSDF_CK(offsets.alloc((size_t)n_chunks + 1));
     const HashMap hmv = hm ? *hm : HashMap{};
-    const float* W = hm ? hm->W : dm->W;
+    const float* W = h16 ? h16->W : (hm ? hm->W : dm->W);
     const float4* A = hm ? hm->A : dm->A;
     const unsigned long long* sorted = hm ? keys.p : nullptr;
     const unsigned cgrid = (unsigned)(n_chunks < (long long)num_sms * 16 ? n_chunks : (long long)num_sms * 16);
@@ -255,7 +283,8 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_sl
     const int dx = dm ? dm->dims[0] : 0, dy = dm ? dm->dims[1] : 0;
     const int ox = dm ? dm->origin[0] : 0, oy = dm ? dm->origin[1] : 0, oz = dm ? dm->origin[2] : 0;
     chunk_write_kernel<<<cgrid, kBlockVoxels, 0, st>>>(sorted, n_chunks, base.p, offsets.p, A, W, dense_voxels,
-                                                       dx, dy, ox, oy, oz, out.p);
+                                                       dx, dy, ox, oy, oz, h16 ? h16->H : nullptr,
+                                                       h16 ? h16->scale : nullptr, out.p);
     GSDF_CK(cudaGetLastError());
     GSDF_CK(cudaStreamSynchronize(st));
     *out_dev = out.release();
@@ -263,10 +292,13 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_sl
     return cudaSuccess;
 }
 
-cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const gsdf_voxel* in_dev, long long n,
-                        int* err, unsigned int* n_blocks, cudaStream_t st, int num_sms) {
+cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, float trunc,
+                        const gsdf_voxel* in_dev, long long n, int* err, unsigned int* n_blocks, cudaStream_t st,
+                        int num_sms) {
     const unsigned grid = (unsigned)(num_sms * 8);
-    if (hm)
+    if (h16)
+        load_kernel_hashed16<<<grid, 256, 0, st>>>(*h16, in_dev, n, trunc, err, n_blocks);
+    else if (hm)
         load_kernel_hashed<<<grid, 256, 0, st>>>(*hm, in_dev, n, err, n_blocks);
     else
         load_kernel_dense<<<grid, 256, 0, st>>>(*dm, in_dev, n, err);

@@ -41,6 +41,11 @@ gsdf_status check_config(const gsdf_config* c) {
     } else {
         return GSDF_ERR_INVALID_ARG;
     }
+    if (c->payload != GSDF_PAYLOAD_F32 && c->payload != GSDF_PAYLOAD_F16) return GSDF_ERR_INVALID_ARG;
+    if (c->payload == GSDF_PAYLOAD_F16) {
+        if (c->grid_kind != GSDF_GRID_HASHED) return GSDF_ERR_INVALID_ARG;
+        if (c->max_touched_blocks < 1 || (long long)c->max_touched_blocks > c->hash_slots) return GSDF_ERR_INVALID_ARG;
+    }
     return GSDF_OK;
 }
 
@@ -61,6 +66,13 @@ gsdf_status check_intr(const gsdf_intrinsics* K, Intr* out) {
     return GSDF_OK;
 }
 
+cudaError_t track_once(const gsdf_handle* h, const float* depth, const Intr& ki, double* T_wc, gsdf_track_stats* stats,
+                       cudaStream_t st) {
+    if (h->fp16) return launch_track16(h->hm16, depth, ki, h->prm, T_wc, stats, h->sc, h->num_sms, st);
+    return launch_track(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, depth, ki, h->prm, T_wc, stats,
+                        h->sc, h->num_sms, st);
+}
+
 gsdf_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return GSDF_OK;
     if (e == cudaErrorMemoryAllocation) return GSDF_ERR_OOM;
@@ -68,6 +80,16 @@ gsdf_status from_cuda(cudaError_t e) {
 }
 
 void free_handle(gsdf_handle* h) {
+    if (h->fp16) {
+        cudaFree(h->hm16.H);
+        cudaFree(h->hm16.W);
+        cudaFree(h->hm16.scale);
+        cudaFree(h->hm16.touch);
+        cudaFree(h->hm16.tlist);
+        cudaFree(h->hm16.tcount);
+        cudaFree(h->hm16.accA);
+        cudaFree(h->hm16.accW);
+    }
     if (h->track_exec) cudaGraphExecDestroy(h->track_exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     cudaFree(h->hm.keys);
@@ -120,13 +142,36 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
     } else {
         h->n_voxels = (long long)cfg->dense_dims[0] * cfg->dense_dims[1] * cfg->dense_dims[2];
     }
-    if (e == cudaSuccess) e = cudaMalloc(&A, sizeof(float4) * (size_t)h->n_voxels);
-    if (e == cudaSuccess) e = cudaMalloc(&W, sizeof(float) * (size_t)h->n_voxels);
+    h->fp16 = cfg->payload == GSDF_PAYLOAD_F16;
+    if (h->fp16) {
+        HashMap16& m = h->hm16;
+        const size_t slots = (size_t)cfg->hash_slots, cap = (size_t)cfg->max_touched_blocks;
+        m.tcap = cfg->max_touched_blocks;
+        if (e == cudaSuccess) e = cudaMalloc(&m.H, sizeof(ushort4) * (size_t)h->n_voxels);
+        if (e == cudaSuccess) e = cudaMalloc(&m.W, sizeof(float) * (size_t)h->n_voxels);
+        if (e == cudaSuccess) e = cudaMalloc(&m.scale, sizeof(float) * slots);
+        if (e == cudaSuccess) e = cudaMalloc(&m.touch, sizeof(int) * slots);
+        if (e == cudaSuccess) e = cudaMalloc(&m.tlist, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&m.tcount, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMalloc(&m.accA, sizeof(float4) * cap * kBlockVoxels);
+        if (e == cudaSuccess) e = cudaMalloc(&m.accW, sizeof(float) * cap * kBlockVoxels);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.H, 0, sizeof(ushort4) * (size_t)h->n_voxels, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.W, 0, sizeof(float) * (size_t)h->n_voxels, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.scale, 0, sizeof(float) * slots, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.touch, 0xFF, sizeof(int) * slots, h->stream);  // -1
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.tcount, 0, sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.accA, 0, sizeof(float4) * cap * kBlockVoxels, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.accW, 0, sizeof(float) * cap * kBlockVoxels, h->stream);
+    } else {
+        if (e == cudaSuccess) e = cudaMalloc(&A, sizeof(float4) * (size_t)h->n_voxels);
+        if (e == cudaSuccess) e = cudaMalloc(&W, sizeof(float) * (size_t)h->n_voxels);
+    }
     if (h->hashed) {
         h->hm.A = A;
         h->hm.W = W;
         h->hm.mask = (unsigned long long)cfg->hash_slots - 1ull;
         h->hm.max_probe = cfg->max_probe;
+        h->hm16.base = h->hm;
     } else {
         h->dm.A = A;
         h->dm.W = W;
@@ -135,8 +180,8 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
             h->dm.origin[i] = cfg->dense_origin[i];
         }
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(A, 0, sizeof(float4) * (size_t)h->n_voxels, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(W, 0, sizeof(float) * (size_t)h->n_voxels, h->stream);
+    if (!h->fp16 && e == cudaSuccess) e = cudaMemsetAsync(A, 0, sizeof(float4) * (size_t)h->n_voxels, h->stream);
+    if (!h->fp16 && e == cudaSuccess) e = cudaMemsetAsync(W, 0, sizeof(float) * (size_t)h->n_voxels, h->stream);
     h->sc.max_track_blocks = 2 * h->num_sms;
     if (e == cudaSuccess) e = cudaMalloc(&h->sc.accum, sizeof(unsigned long long) * kAccumWords);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->sc.accum, 0, sizeof(unsigned long long) * kAccumWords, h->stream);
@@ -189,6 +234,9 @@ gsdf_status gsdf_integrate(gsdf_handle* h, const float* depth_dev, const gsdf_in
     Intr ki;
     gsdf_status s = check_intr(K, &ki);
     if (s != GSDF_OK) return s;
+    if (h->fp16)
+        return from_cuda(launch_integrate16(h->hm16, depth_dev, ki, h->prm, T_wc_dev, stats_dev, h->sc, h->num_sms,
+                                            h->stream));
     return from_cuda(launch_integrate(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, depth_dev, ki,
                                       h->prm, T_wc_dev, stats_dev, h->sc, h->stream));
 }
@@ -199,8 +247,7 @@ gsdf_status gsdf_track_step(gsdf_handle* h, const float* depth_dev, const gsdf_i
     Intr ki;
     gsdf_status s = check_intr(K, &ki);
     if (s != GSDF_OK) return s;
-    return from_cuda(launch_track(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, depth_dev, ki,
-                                  h->prm, T_wc_dev, stats_dev, h->sc, h->num_sms, h->stream));
+    return from_cuda(track_once(h, depth_dev, ki, T_wc_dev, stats_dev, h->stream));
 }
 
 gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K, double* T_wc_dev,
@@ -209,15 +256,12 @@ gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrin
     Intr ki;
     gsdf_status s = check_intr(K, &ki);
     if (s != GSDF_OK) return s;
-    const DenseMap* dm = h->hashed ? nullptr : &h->dm;
-    const HashMap* hm = h->hashed ? &h->hm : nullptr;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
     if (e != cudaSuccess) return from_cuda(e);
     if (cs != cudaStreamCaptureStatusNone) {  // the caller is capturing: launch into its graph
         for (int it = 0; it < n_iters && e == cudaSuccess; ++it)
-            e = launch_track(dm, hm, depth_dev, ki, h->prm, T_wc_dev, stats_dev ? stats_dev + it : nullptr, h->sc,
-                             h->num_sms, h->stream);
+            e = track_once(h, depth_dev, ki, T_wc_dev, stats_dev ? stats_dev + it : nullptr, h->stream);
         return from_cuda(e);
     }
     const bool same = h->track_exec && h->g_depth == depth_dev && h->g_pose == T_wc_dev && h->g_stats == stats_dev &&
@@ -232,8 +276,7 @@ gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrin
         if (e != cudaSuccess) return from_cuda(e);
         cudaError_t le = cudaSuccess;
         for (int it = 0; it < n_iters && le == cudaSuccess; ++it)
-            le = launch_track(dm, hm, depth_dev, ki, h->prm, T_wc_dev, stats_dev ? stats_dev + it : nullptr, h->sc,
-                              h->num_sms, h->capture_stream);
+            le = track_once(h, depth_dev, ki, T_wc_dev, stats_dev ? stats_dev + it : nullptr, h->capture_stream);
         e = cudaStreamEndCapture(h->capture_stream, &graph);
         if (le != cudaSuccess) e = le;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&h->track_exec, graph, 0);
@@ -256,7 +299,7 @@ gsdf_status gsdf_extract_voxels(gsdf_handle* h, gsdf_voxel* host_out, size_t cap
     if (!h || !count_out || (capacity > 0 && !host_out)) return GSDF_ERR_INVALID_ARG;
     gsdf_voxel* dev = nullptr;
     long long n = 0;
-    cudaError_t e = extract_voxels(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr,
+    cudaError_t e = extract_voxels(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, h->fp16 ? &h->hm16 : nullptr,
                                    h->hashed ? h->cfg.hash_slots : 0, h->stream, h->num_sms, &dev, &n);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -280,8 +323,8 @@ gsdf_status gsdf_load_voxels(gsdf_handle* h, const gsdf_voxel* host_in, size_t n
     cudaError_t e = cudaMalloc(&dev, sizeof(gsdf_voxel) * n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dev, host_in, sizeof(gsdf_voxel) * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = load_voxels(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, dev, (long long)n, h->sc.err,
-                        h->sc.n_blocks, h->stream, h->num_sms);
+        e = load_voxels(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, h->fp16 ? &h->hm16 : nullptr,
+                        h->prm.trunc, dev, (long long)n, h->sc.err, h->sc.n_blocks, h->stream, h->num_sms);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(dev);
     if (e != cudaSuccess) {

@@ -10,6 +10,7 @@
 //   psi = A.x / W when read.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -95,6 +96,17 @@ struct DenseMap {
                                                         unsigned int* /*n_new*/) const {
         return find(mx, my, mz);
     }
+    // psi and the (unnormalised) gradient of voxel idx; false if unobserved (W = 0)
+    __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
+        const float w = __ldg(W + idx);
+        if (!(w > 0.0f)) return false;
+        const float4 a = __ldg(A + idx);
+        psi = __fdividef(a.x, w);
+        gx = a.y;
+        gy = a.z;
+        gz = a.w;
+        return true;
+    }
 };
 
 struct HashMap {
@@ -152,7 +164,80 @@ struct HashMap {
         atomicCAS(err, kErrNone, (int)GSDF_ERR_CAPACITY);
         return -1;
     }
+    __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
+        const float w = __ldg(W + idx);
+        if (!(w > 0.0f)) return false;
+        const float4 a = __ldg(A + idx);
+        psi = __fdividef(a.x, w);
+        gx = a.y;
+        gy = a.z;
+        gz = a.w;
+        return true;
+    }
 };
+
+// FP16 payload on the same 8^3-block hash table.  Per voxel: half4 (psi / sigma_b, gbar) with
+// gbar = g / W (|gbar| <= 1, same direction as g), and W in FP32; per block: sigma_b, a scale that
+// only grows (the largest |psi| the block has held).  A frame is fused in two passes: the ray march
+// adds (w d, w n, w) into FP32 accumulators of the blocks it touches (a compact per-frame list),
+// then one CTA per touched block folds them in with Eq. (sdf_update) / (gradient_update) and
+// re-encodes (round to nearest).
+struct HashMap16 {
+    HashMap base;      // keys, mask, probe limit (its A and W are unused)
+    ushort4* H;        // [slots * 512] half bits of (psi / sigma_b, gbar_x, gbar_y, gbar_z)
+    float* W;          // [slots * 512]
+    float* scale;      // [slots] sigma_b
+    int* touch;        // [slots] -1 untouched this frame, -2 being claimed, >= 0 accumulator block
+    int* tlist;        // [tcap] slots touched this frame, in claim order
+    unsigned int* tcount;
+    int tcap;
+    float4* accA;      // [tcap * 512] (sum w d, sum w n)
+    float* accW;       // [tcap * 512] sum w
+
+    __device__ __forceinline__ long long find(int mx, int my, int mz) const { return base.find(mx, my, mz); }
+    __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
+        const float w = __ldg(W + idx);
+        if (!(w > 0.0f)) return false;
+        const ushort4 h = __ldg(H + idx);
+        psi = __half2float(__ushort_as_half(h.x)) * __ldg(scale + (idx >> 9));
+        gx = __half2float(__ushort_as_half(h.y));
+        gy = __half2float(__ushort_as_half(h.z));
+        gz = __half2float(__ushort_as_half(h.w));
+        return true;
+    }
+};
+
+constexpr int kClaimSpinLimit = 1 << 20;  // bounded wait for another thread's block claim
+
+// Accumulator block of hash slot `slot` for this frame: the first claimant takes the next entry of
+// the touched list; others wait (bounded) until it is published.  -1 on capacity or timeout
+// (recorded in err).
+__device__ __forceinline__ int claim_block(const HashMap16& m, long long slot, int* err) {
+    int v = __ldcg(m.touch + slot);
+    if (v >= 0) return v;
+    if (v == -1) {
+        v = atomicCAS(m.touch + slot, -1, -2);
+        if (v == -1) {
+            const unsigned ci = atomicAdd(m.tcount, 1u);
+            if (ci >= (unsigned)m.tcap) {
+                atomicExch(m.touch + slot, -1);
+                atomicCAS(err, kErrNone, (int)GSDF_ERR_CAPACITY);
+                return -1;
+            }
+            m.tlist[ci] = (int)slot;
+            __threadfence();
+            atomicExch(m.touch + slot, (int)ci);
+            return (int)ci;
+        }
+    }
+    for (int it = 0; it < kClaimSpinLimit && v == -2; ++it) {
+        __nanosleep(32);
+        v = atomicAdd(m.touch + slot, 0);
+    }
+    if (v >= 0) return v;
+    if (v == -2) atomicCAS(err, kErrNone, (int)GSDF_ERR_TIMEOUT);
+    return -1;
+}
 
 // ------------------------------------------------------------------------------------------
 // FP32 index path: correctly rounded operations in a fixed order, no contraction, so that every
@@ -230,6 +315,13 @@ cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* dep
                          const Params& prm, double* T_wc, gsdf_track_stats* stats,
                          const Scratch& sc, int num_sms, cudaStream_t st);
 
+cudaError_t launch_track16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                           gsdf_track_stats* stats, const Scratch& sc, int num_sms, cudaStream_t st);
+
+cudaError_t launch_integrate16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm,
+                               const double* T_wc, gsdf_integrate_stats* stats, const Scratch& sc, int num_sms,
+                               cudaStream_t st);
+
 cudaError_t launch_integrate(const DenseMap* dm, const HashMap* hm, const float* depth,
                              const Intr& K, const Params& prm, const double* T_wc,
                              gsdf_integrate_stats* stats, const Scratch& sc, cudaStream_t st);
@@ -238,15 +330,18 @@ cudaError_t launch_integrate(const DenseMap* dm, const HashMap* hm, const float*
 
 namespace gsdf {
 // extraction / checkpoint (extract.cu).  *out_dev is allocated with cudaMalloc; caller frees.
-cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, long long n_slots, cudaStream_t st,
-                           int num_sms, gsdf_voxel** out_dev, long long* n_out);
-cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const gsdf_voxel* in_dev, long long n,
-                        int* err, unsigned int* n_blocks, cudaStream_t st, int num_sms);
+cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
+                           cudaStream_t st, int num_sms, gsdf_voxel** out_dev, long long* n_out);
+cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, float trunc,
+                        const gsdf_voxel* in_dev, long long n, int* err, unsigned int* n_blocks, cudaStream_t st,
+                        int num_sms);
 }  // namespace gsdf
 
 // A map handle (the C ABI's opaque gsdf_handle).
 struct gsdf_handle {
     gsdf_config cfg;
+    bool fp16;
+    gsdf::HashMap16 hm16;  // FP16 payload (hashed maps with GSDF_PAYLOAD_F16)
     cudaStream_t stream;
     int device;
     int num_sms;

@@ -53,8 +53,85 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
     }
 }
 
+// FP16 maps, second pass: one CTA per touched block folds the frame's sums into its voxels with
+// Eqs. (sdf_update) and (gradient_update), in FP32:
+//   W' = W + S_w,  psi' = (W psi + S_d) / W',  gbar' = (W gbar + S_n) / W',
+// grows the block scale to max(sigma_b, max |psi'|) and re-encodes (psi' / sigma_b', gbar') to
+// FP16 with round-to-nearest.  Untouched voxels of the block keep their bits unless the scale grew.
+// The accumulators and the touched marks are cleared for the next frame.
+__global__ void __launch_bounds__(kBlockVoxels) apply16_kernel(HashMap16 m, float trunc) {
+    __shared__ float red[kBlockVoxels / 32];
+    const unsigned n = min(*m.tcount, (unsigned)m.tcap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (unsigned ci = blockIdx.x; ci < n; ci += gridDim.x) {
+        const int slot = m.tlist[ci];
+        const long long gi = (long long)slot * kBlockVoxels + threadIdx.x;
+        const long long ai = (long long)ci * kBlockVoxels + threadIdx.x;
+        const float sw = m.accW[ai];
+        const float4 sa = m.accA[ai];
+        const ushort4 h = m.H[gi];
+        float w = m.W[gi];
+        const float sigma = m.scale[slot];
+        float psi = __half2float(__ushort_as_half(h.x)) * sigma;
+        float g0 = __half2float(__ushort_as_half(h.y));
+        float g1 = __half2float(__ushort_as_half(h.z));
+        float g2 = __half2float(__ushort_as_half(h.w));
+        if (sw > 0.0f) {
+            const float wn = w + sw;
+            psi = (w * psi + sa.x) / wn;
+            g0 = (w * g0 + sa.y) / wn;
+            g1 = (w * g1 + sa.z) / wn;
+            g2 = (w * g2 + sa.w) / wn;
+            w = wn;
+        }
+        float amax = w > 0.0f ? fabsf(psi) : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (lane == 0) red[warp] = amax;
+        __syncthreads();
+        float bmax = red[0];
+#pragma unroll
+        for (int k = 1; k < kBlockVoxels / 32; ++k) bmax = fmaxf(bmax, red[k]);
+        float sig = fmaxf(sigma, bmax);
+        if (!(sig > 0.0f)) sig = trunc;  // nothing observed yet: any positive scale encodes zeros
+        ushort4 o4;
+        o4.x = __half_as_ushort(__float2half_rn(w > 0.0f ? psi / sig : 0.0f));
+        o4.y = __half_as_ushort(__float2half_rn(g0));
+        o4.z = __half_as_ushort(__float2half_rn(g1));
+        o4.w = __half_as_ushort(__float2half_rn(g2));
+        m.H[gi] = o4;
+        m.W[gi] = w;
+        m.accA[ai] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        m.accW[ai] = 0.0f;
+        if (threadIdx.x == 0) {
+            m.scale[slot] = sig;
+            m.touch[slot] = -1;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void integrate_stats_total(gsdf_integrate_stats* stats, const unsigned int* n_blocks) {
     stats->n_blocks_total = (long long)*n_blocks;
+}
+
+cudaError_t launch_integrate16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm,
+                               const double* T_wc, gsdf_integrate_stats* stats, const Scratch& sc, int num_sms,
+                               cudaStream_t st) {
+    if (stats) {
+        cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(gsdf_integrate_stats), st);
+        if (e != cudaSuccess) return e;
+    }
+    const long long n_px = (long long)K.width * K.height;
+    const unsigned blocks = (unsigned)((n_px + kIntThreads - 1) / kIntThreads);
+    integrate_kernel<HashMap16><<<blocks, kIntThreads, 0, st>>>(hm, depth, K, prm, T_wc, stats, sc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    apply16_kernel<<<2 * num_sms, kBlockVoxels, 0, st>>>(hm, prm.trunc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(hm.tcount, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    if (stats) integrate_stats_total<<<1, 1, 0, st>>>(stats, sc.n_blocks);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_integrate(const DenseMap* dm, const HashMap* hm, const float* depth,

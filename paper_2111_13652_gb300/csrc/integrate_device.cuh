@@ -78,6 +78,40 @@ __device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, in
     return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
 }
 
+// FP16 maps: the index returned addresses the frame's accumulators (claimed block * 512 + local)
+template <>
+__device__ __forceinline__ long long voxel_index<HashMap16>(const HashMap16& map, int mx, int my, int mz,
+                                                            BlockCache& bc, int* err, unsigned int* n_new) {
+    const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
+    if (bx != bc.bx || by != bc.by || bz != bc.bz) {
+        const long long idx = map.base.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
+        bc.bx = bx;
+        bc.by = by;
+        bc.bz = bz;
+        bc.base = -1;
+        if (idx >= 0) {
+            const int ci = claim_block(map, idx >> 9, err);
+            if (ci >= 0) bc.base = (long long)ci * kBlockVoxels;
+        }
+    }
+    if (bc.base < 0) return -1;
+    return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
+}
+
+// (w d, w n) and w of one visit
+__device__ __forceinline__ void scatter(const DenseMap& m, long long i, float4 v, float w) {
+    atomicAdd(m.A + i, v);
+    atomicAdd(m.W + i, w);
+}
+__device__ __forceinline__ void scatter(const HashMap& m, long long i, float4 v, float w) {
+    atomicAdd(m.A + i, v);
+    atomicAdd(m.W + i, w);
+}
+__device__ __forceinline__ void scatter(const HashMap16& m, long long i, float4 v, float w) {
+    atomicAdd(m.accA + i, v);
+    atomicAdd(m.accW + i, w);
+}
+
 template <>
 __device__ __forceinline__ long long voxel_index<DenseMap>(const DenseMap& map, int mx, int my, int mz, BlockCache&,
                                                            int*, unsigned int*) {
@@ -138,8 +172,7 @@ __device__ __forceinline__ void integrate_ray(const Map& map, const float* __res
         if (!(w > 0.0f)) continue;
         const long long idx = voxel_index(map, mx, my, mz, bc, err, n_new);
         if (idx < 0) continue;
-        atomicAdd(map.A + idx, make_float4(w * d, w * nwx, w * nwy, w * nwz));
-        atomicAdd(map.W + idx, w);
+        scatter(map, idx, make_float4(w * d, w * nwx, w * nwy, w * nwz), w);
         ++visits;
     }
 }

@@ -31,6 +31,18 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
     finish_scene(sh, sc.accum, sc.counter, prm, T_wc, stats);
 }
 
+cudaError_t launch_track16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                           gsdf_track_stats* stats, const Scratch& sc, int num_sms, cudaStream_t st) {
+    const long long n_px = (long long)K.width * K.height;
+    long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
+    long long cap = (long long)kTrackBlocksPerSM * num_sms;
+    if (cap > sc.max_track_blocks) cap = sc.max_track_blocks;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    track_kernel<HashMap16><<<(unsigned)blocks, kTrackThreads, 0, st>>>(hm, depth, K, prm, T_wc, stats, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
                          const Params& prm, double* T_wc, gsdf_track_stats* stats,
                          const Scratch& sc, int num_sms, cudaStream_t st) {

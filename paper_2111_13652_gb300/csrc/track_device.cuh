@@ -286,14 +286,12 @@ __device__ __forceinline__ void track_pixel(const Map& map, const float* __restr
     const int mz = round_voxel(P[2], prm.inv_vs);
     const long long idx = map.find(mx, my, mz);
     if (idx < 0) return;
-    const float W = __ldg(map.W + idx);
-    if (!(W > 0.0f)) return;
-    const float4 a = __ldg(map.A + idx);
-    const float gn2 = a.y * a.y + a.z * a.z + a.w * a.w;
+    float psi, g0, g1, g2;
+    if (!map.voxel(idx, psi, g0, g1, g2)) return;
+    const float gn2 = g0 * g0 + g1 * g1 + g2 * g2;
     if (!(gn2 > 0.0f)) return;
     const float inv_gn = rsqrtf(gn2);
-    const float gx = a.y * inv_gn, gy = a.z * inv_gn, gz = a.w * inv_gn;
-    const float psi = __fdividef(a.x, W);
+    const float gx = g0 * inv_gn, gy = g1 * inv_gn, gz = g2 * inv_gn;
     // P - v_s m with a single rounding per component
     const float dx = fmaf(-(float)mx, prm.vs, P[0]);
     const float dy = fmaf(-(float)my, prm.vs, P[1]);

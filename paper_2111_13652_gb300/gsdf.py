@@ -25,6 +25,8 @@ GSDF_ERR_TIMEOUT = 6
 GSDF_ERR_NO_VALID_PIXELS = 7
 GSDF_GRID_DENSE = 0
 GSDF_GRID_HASHED = 1
+GSDF_PAYLOAD_F32 = 0
+GSDF_PAYLOAD_F16 = 1
 
 
 class gsdf_intrinsics(C.Structure):
@@ -36,7 +38,8 @@ class gsdf_config(C.Structure):
     _fields_ = [("grid_kind", C.c_int32), ("dense_dims", C.c_int32 * 3), ("dense_origin", C.c_int32 * 3),
                 ("voxel_size", C.c_float), ("truncation", C.c_float), ("weight_eps", C.c_float),
                 ("huber_delta", C.c_float), ("cos_max_angle", C.c_float), ("damping", C.c_double),
-                ("hash_slots", C.c_int64), ("max_probe", C.c_int32), ("reserved", C.c_int32)]
+                ("hash_slots", C.c_int64), ("max_probe", C.c_int32), ("payload", C.c_int32),
+                ("max_touched_blocks", C.c_int32), ("pad", C.c_int32)]
 
 
 class gsdf_track_stats(C.Structure):
@@ -206,7 +209,7 @@ def intrinsics(cam) -> gsdf_intrinsics:
 
 def make_config(voxel_size, *, dense_dims=None, dense_origin=(0, 0, 0), truncation=None, weight_eps=None,
                 huber_delta=None, cos_max_angle=0.25881904, damping=0.0, hash_slots=1 << 16,
-                max_probe=128) -> gsdf_config:
+                max_probe=128, fp16=False, max_touched_blocks=None) -> gsdf_config:
     vs = float(voxel_size)
     c = gsdf_config()
     c.grid_kind = GSDF_GRID_HASHED if dense_dims is None else GSDF_GRID_DENSE
@@ -221,6 +224,8 @@ def make_config(voxel_size, *, dense_dims=None, dense_origin=(0, 0, 0), truncati
     c.damping = damping
     c.hash_slots = hash_slots
     c.max_probe = max_probe
+    c.payload = GSDF_PAYLOAD_F16 if fp16 else GSDF_PAYLOAD_F32
+    c.max_touched_blocks = max(1, hash_slots // 4) if max_touched_blocks is None else max_touched_blocks
     return c
 
 
