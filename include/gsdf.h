@@ -87,8 +87,10 @@ typedef struct {
  *                  arithmetic stays FP32; a frame is fused into FP32 accumulators of the touched
  *                  blocks, then folded into them and re-encoded with round-to-nearest, so psi
  *                  carries an error of at most 2^-11 sigma_b per frame and ghat about 5e-4.
- *   max_touched_blocks  FP16 payload only: capacity of the per-frame accumulators, in blocks;
- *                  a frame touching more blocks is fused partially and reports GSDF_ERR_CAPACITY */
+ *   max_touched_blocks  FP16 payload only: entries of the per-frame accumulator table (a power
+ *                  of two, at most hash_slots; keep it at least twice the blocks one frame
+ *                  touches).  A frame whose blocks do not find an entry within 64 probes is fused
+ *                  partially and reports GSDF_ERR_CAPACITY */
 typedef struct {
     int32_t grid_kind;
     int32_t dense_dims[3];

@@ -44,7 +44,8 @@ gsdf_status check_config(const gsdf_config* c) {
     if (c->payload != GSDF_PAYLOAD_F32 && c->payload != GSDF_PAYLOAD_F16) return GSDF_ERR_INVALID_ARG;
     if (c->payload == GSDF_PAYLOAD_F16) {
         if (c->grid_kind != GSDF_GRID_HASHED) return GSDF_ERR_INVALID_ARG;
-        if (c->max_touched_blocks < 1 || (long long)c->max_touched_blocks > c->hash_slots) return GSDF_ERR_INVALID_ARG;
+        const long long a = c->max_touched_blocks;
+        if (a < 1 || a > c->hash_slots || (a & (a - 1)) != 0) return GSDF_ERR_INVALID_ARG;
     }
     return GSDF_OK;
 }
@@ -84,9 +85,9 @@ void free_handle(gsdf_handle* h) {
         cudaFree(h->hm16.H);
         cudaFree(h->hm16.W);
         cudaFree(h->hm16.scale);
-        cudaFree(h->hm16.touch);
-        cudaFree(h->hm16.tlist);
-        cudaFree(h->hm16.tcount);
+        cudaFree(h->hm16.akeys);
+        cudaFree(h->hm16.alist);
+        cudaFree(h->hm16.acount);
         cudaFree(h->hm16.accA);
         cudaFree(h->hm16.accW);
     }
@@ -146,20 +147,20 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
     if (h->fp16) {
         HashMap16& m = h->hm16;
         const size_t slots = (size_t)cfg->hash_slots, cap = (size_t)cfg->max_touched_blocks;
-        m.tcap = cfg->max_touched_blocks;
+        m.amask = (unsigned int)cap - 1u;
         if (e == cudaSuccess) e = cudaMalloc(&m.H, sizeof(ushort4) * (size_t)h->n_voxels);
         if (e == cudaSuccess) e = cudaMalloc(&m.W, sizeof(float) * (size_t)h->n_voxels);
         if (e == cudaSuccess) e = cudaMalloc(&m.scale, sizeof(float) * slots);
-        if (e == cudaSuccess) e = cudaMalloc(&m.touch, sizeof(int) * slots);
-        if (e == cudaSuccess) e = cudaMalloc(&m.tlist, sizeof(int) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&m.tcount, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMalloc(&m.akeys, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&m.alist, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&m.acount, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.acount, 0, sizeof(unsigned int), h->stream);
         if (e == cudaSuccess) e = cudaMalloc(&m.accA, sizeof(float4) * cap * kBlockVoxels);
         if (e == cudaSuccess) e = cudaMalloc(&m.accW, sizeof(float) * cap * kBlockVoxels);
         if (e == cudaSuccess) e = cudaMemsetAsync(m.H, 0, sizeof(ushort4) * (size_t)h->n_voxels, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(m.W, 0, sizeof(float) * (size_t)h->n_voxels, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(m.scale, 0, sizeof(float) * slots, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(m.touch, 0xFF, sizeof(int) * slots, h->stream);  // -1
-        if (e == cudaSuccess) e = cudaMemsetAsync(m.tcount, 0, sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m.akeys, 0xFF, sizeof(int) * cap, h->stream);  // -1 = free
         if (e == cudaSuccess) e = cudaMemsetAsync(m.accA, 0, sizeof(float4) * cap * kBlockVoxels, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(m.accW, 0, sizeof(float) * cap * kBlockVoxels, h->stream);
     } else {

@@ -179,20 +179,20 @@ struct HashMap {
 // FP16 payload on the same 8^3-block hash table.  Per voxel: half4 (psi / sigma_b, gbar) with
 // gbar = g / W (|gbar| <= 1, same direction as g), and W in FP32; per block: sigma_b, a scale that
 // only grows (the largest |psi| the block has held).  A frame is fused in two passes: the ray march
-// adds (w d, w n, w) into FP32 accumulators of the blocks it touches (a compact per-frame list),
-// then one CTA per touched block folds them in with Eq. (sdf_update) / (gradient_update) and
-// re-encodes (round to nearest).
+// adds (w d, w n, w) into FP32 accumulators of the blocks it touches, kept in a small
+// open-addressing table keyed by hash slot, then one CTA per occupied accumulator entry folds them
+// in with Eq. (sdf_update) / (gradient_update) and re-encodes (round to nearest).
 struct HashMap16 {
     HashMap base;      // keys, mask, probe limit (its A and W are unused)
     ushort4* H;        // [slots * 512] half bits of (psi / sigma_b, gbar_x, gbar_y, gbar_z)
     float* W;          // [slots * 512]
     float* scale;      // [slots] sigma_b
-    int* touch;        // [slots] -1 untouched this frame, -2 being claimed, >= 0 accumulator block
-    int* tlist;        // [tcap] slots touched this frame, in claim order
-    unsigned int* tcount;
-    int tcap;
-    float4* accA;      // [tcap * 512] (sum w d, sum w n)
-    float* accW;       // [tcap * 512] sum w
+    int* akeys;        // [acap] hash slot owning each accumulator entry, -1 = free
+    unsigned int amask;  // acap - 1 (acap a power of two)
+    float4* accA;      // [acap * 512] (sum w d, sum w n)
+    float* accW;       // [acap * 512] sum w
+    int* alist;        // [acap] occupied entries, listed by the apply pass
+    unsigned int* acount;
 
     __device__ __forceinline__ long long find(int mx, int my, int mz) const { return base.find(mx, my, mz); }
     __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
@@ -207,35 +207,23 @@ struct HashMap16 {
     }
 };
 
-constexpr int kClaimSpinLimit = 1 << 20;  // bounded wait for another thread's block claim
+constexpr int kAccProbeLimit = 64;
 
-// Accumulator block of hash slot `slot` for this frame: the first claimant takes the next entry of
-// the touched list; others wait (bounded) until it is published.  -1 on capacity or timeout
-// (recorded in err).
-__device__ __forceinline__ int claim_block(const HashMap16& m, long long slot, int* err) {
-    int v = __ldcg(m.touch + slot);
-    if (v >= 0) return v;
-    if (v == -1) {
-        v = atomicCAS(m.touch + slot, -1, -2);
+// Accumulator entry of hash slot `slot` for this frame, inserted on first use with one
+// compare-and-swap (entries are only freed by the apply pass, so no reader ever waits).  -1 when
+// the probe limit is reached (recorded as GSDF_ERR_CAPACITY).
+__device__ __forceinline__ int acc_entry(const HashMap16& m, long long slot, int* err) {
+    unsigned int p = (unsigned int)mix64((unsigned long long)slot) & m.amask;
+    for (int k = 0; k < kAccProbeLimit; ++k) {
+        int v = __ldcg(m.akeys + p);
         if (v == -1) {
-            const unsigned ci = atomicAdd(m.tcount, 1u);
-            if (ci >= (unsigned)m.tcap) {
-                atomicExch(m.touch + slot, -1);
-                atomicCAS(err, kErrNone, (int)GSDF_ERR_CAPACITY);
-                return -1;
-            }
-            m.tlist[ci] = (int)slot;
-            __threadfence();
-            atomicExch(m.touch + slot, (int)ci);
-            return (int)ci;
+            v = atomicCAS(m.akeys + p, -1, (int)slot);
+            if (v == -1) return (int)p;
         }
+        if (v == (int)slot) return (int)p;
+        p = (p + 1) & m.amask;
     }
-    for (int it = 0; it < kClaimSpinLimit && v == -2; ++it) {
-        __nanosleep(32);
-        v = atomicAdd(m.touch + slot, 0);
-    }
-    if (v >= 0) return v;
-    if (v == -2) atomicCAS(err, kErrNone, (int)GSDF_ERR_TIMEOUT);
+    atomicCAS(err, kErrNone, (int)GSDF_ERR_CAPACITY);
     return -1;
 }
 

@@ -53,58 +53,91 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
     }
 }
 
-// FP16 maps, second pass: one CTA per touched block folds the frame's sums into its voxels with
-// Eqs. (sdf_update) and (gradient_update), in FP32:
+// FP16 maps, second pass.  The occupied accumulator entries are listed first; then one block per
+// listed entry folds the frame's sums into the voxels that received updates, with Eqs.
+// (sdf_update) and (gradient_update) in FP32:
 //   W' = W + S_w,  psi' = (W psi + S_d) / W',  gbar' = (W gbar + S_n) / W',
-// grows the block scale to max(sigma_b, max |psi'|) and re-encodes (psi' / sigma_b', gbar') to
-// FP16 with round-to-nearest.  Untouched voxels of the block keep their bits unless the scale grew.
-// The accumulators and the touched marks are cleared for the next frame.
-__global__ void __launch_bounds__(kBlockVoxels) apply16_kernel(HashMap16 m, float trunc) {
-    __shared__ float red[kBlockVoxels / 32];
-    const unsigned n = min(*m.tcount, (unsigned)m.tcap);
+// and re-encodes them (psi' / sigma_b, gbar') to FP16 with round-to-nearest.  The block scale
+// becomes max(sigma_b, max |psi'| over the updated voxels); the other voxels already satisfy
+// |psi| <= sigma_b, so only when the scale grows are they re-encoded too.  The entry's
+// accumulators are cleared and the entry freed for the next frame.
+__global__ void list16_kernel(HashMap16 m) {
+    const unsigned n = m.amask + 1u;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        if (m.akeys[e] >= 0) m.alist[atomicAdd(m.acount, 1u)] = (int)e;
+}
+
+constexpr int kApplyThreads = 256;
+constexpr int kApplyPer = kBlockVoxels / kApplyThreads;
+
+__global__ void __launch_bounds__(kApplyThreads) apply16_kernel(HashMap16 m, float trunc) {
+    __shared__ float red[kApplyThreads / 32];
+    const unsigned cnt = *m.acount;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (unsigned ci = blockIdx.x; ci < n; ci += gridDim.x) {
-        const int slot = m.tlist[ci];
-        const long long gi = (long long)slot * kBlockVoxels + threadIdx.x;
-        const long long ai = (long long)ci * kBlockVoxels + threadIdx.x;
-        const float sw = m.accW[ai];
-        const float4 sa = m.accA[ai];
-        const ushort4 h = m.H[gi];
-        float w = m.W[gi];
+    for (unsigned q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const unsigned ci = (unsigned)m.alist[q];
+        const int slot = m.akeys[ci];
         const float sigma = m.scale[slot];
-        float psi = __half2float(__ushort_as_half(h.x)) * sigma;
-        float g0 = __half2float(__ushort_as_half(h.y));
-        float g1 = __half2float(__ushort_as_half(h.z));
-        float g2 = __half2float(__ushort_as_half(h.w));
-        if (sw > 0.0f) {
-            const float wn = w + sw;
-            psi = (w * psi + sa.x) / wn;
-            g0 = (w * g0 + sa.y) / wn;
-            g1 = (w * g1 + sa.z) / wn;
-            g2 = (w * g2 + sa.w) / wn;
-            w = wn;
+        const long long gbase = (long long)slot * kBlockVoxels, abase = (long long)ci * kBlockVoxels;
+        float psi[kApplyPer], g0[kApplyPer], g1[kApplyPer], g2[kApplyPer], w[kApplyPer], sw[kApplyPer];
+        float4 sa[kApplyPer];
+        ushort4 h[kApplyPer];
+#pragma unroll
+        for (int k = 0; k < kApplyPer; ++k) {
+            const int v = threadIdx.x + k * kApplyThreads;
+            sw[k] = m.accW[abase + v];
+            sa[k] = m.accA[abase + v];
+            h[k] = m.H[gbase + v];
+            w[k] = m.W[gbase + v];
         }
-        float amax = w > 0.0f ? fabsf(psi) : 0.0f;
+        float amax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kApplyPer; ++k) {
+            psi[k] = __half2float(__ushort_as_half(h[k].x)) * sigma;
+            g0[k] = __half2float(__ushort_as_half(h[k].y));
+            g1[k] = __half2float(__ushort_as_half(h[k].z));
+            g2[k] = __half2float(__ushort_as_half(h[k].w));
+            if (sw[k] > 0.0f) {
+                const float wn = w[k] + sw[k];
+                psi[k] = (w[k] * psi[k] + sa[k].x) / wn;
+                g0[k] = (w[k] * g0[k] + sa[k].y) / wn;
+                g1[k] = (w[k] * g1[k] + sa[k].z) / wn;
+                g2[k] = (w[k] * g2[k] + sa[k].w) / wn;
+                w[k] = wn;
+                amax = fmaxf(amax, fabsf(psi[k]));
+            }
+        }
         for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         if (lane == 0) red[warp] = amax;
         __syncthreads();
         float bmax = red[0];
 #pragma unroll
-        for (int k = 1; k < kBlockVoxels / 32; ++k) bmax = fmaxf(bmax, red[k]);
+        for (int k = 1; k < kApplyThreads / 32; ++k) bmax = fmaxf(bmax, red[k]);
         float sig = fmaxf(sigma, bmax);
         if (!(sig > 0.0f)) sig = trunc;  // nothing observed yet: any positive scale encodes zeros
-        ushort4 o4;
-        o4.x = __half_as_ushort(__float2half_rn(w > 0.0f ? psi / sig : 0.0f));
-        o4.y = __half_as_ushort(__float2half_rn(g0));
-        o4.z = __half_as_ushort(__float2half_rn(g1));
-        o4.w = __half_as_ushort(__float2half_rn(g2));
-        m.H[gi] = o4;
-        m.W[gi] = w;
-        m.accA[ai] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        m.accW[ai] = 0.0f;
+        const bool rescale = sig != sigma && sigma > 0.0f;
+#pragma unroll
+        for (int k = 0; k < kApplyPer; ++k) {
+            const int v = threadIdx.x + k * kApplyThreads;
+            if (sw[k] > 0.0f) {
+                ushort4 o4;
+                o4.x = __half_as_ushort(__float2half_rn(psi[k] / sig));
+                o4.y = __half_as_ushort(__float2half_rn(g0[k]));
+                o4.z = __half_as_ushort(__float2half_rn(g1[k]));
+                o4.w = __half_as_ushort(__float2half_rn(g2[k]));
+                m.H[gbase + v] = o4;
+                m.W[gbase + v] = w[k];
+                m.accA[abase + v] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                m.accW[abase + v] = 0.0f;
+            } else if (rescale) {
+                ushort4 hh = h[k];
+                hh.x = __half_as_ushort(__float2half_rn(psi[k] / sig));
+                m.H[gbase + v] = hh;
+            }
+        }
         if (threadIdx.x == 0) {
             m.scale[slot] = sig;
-            m.touch[slot] = -1;
+            m.akeys[ci] = -1;
         }
         __syncthreads();
     }
@@ -126,9 +159,10 @@ cudaError_t launch_integrate16(const HashMap16& hm, const float* depth, const In
     integrate_kernel<HashMap16><<<blocks, kIntThreads, 0, st>>>(hm, depth, K, prm, T_wc, stats, sc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    apply16_kernel<<<2 * num_sms, kBlockVoxels, 0, st>>>(hm, prm.trunc);
+    list16_kernel<<<2 * num_sms, 256, 0, st>>>(hm);
+    apply16_kernel<<<16 * num_sms, kApplyThreads, 0, st>>>(hm, prm.trunc);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemsetAsync(hm.tcount, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hm.acount, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     if (stats) integrate_stats_total<<<1, 1, 0, st>>>(stats, sc.n_blocks);
     return cudaGetLastError();

@@ -78,7 +78,7 @@ __device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, in
     return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
 }
 
-// FP16 maps: the index returned addresses the frame's accumulators (claimed block * 512 + local)
+// FP16 maps: the index returned addresses the frame's accumulators (entry * 512 + local)
 template <>
 __device__ __forceinline__ long long voxel_index<HashMap16>(const HashMap16& map, int mx, int my, int mz,
                                                             BlockCache& bc, int* err, unsigned int* n_new) {
@@ -90,7 +90,7 @@ __device__ __forceinline__ long long voxel_index<HashMap16>(const HashMap16& map
         bc.bz = bz;
         bc.base = -1;
         if (idx >= 0) {
-            const int ci = claim_block(map, idx >> 9, err);
+            const int ci = acc_entry(map, idx >> 9, err);
             if (ci >= 0) bc.base = (long long)ci * kBlockVoxels;
         }
     }

@@ -225,7 +225,7 @@ def make_config(voxel_size, *, dense_dims=None, dense_origin=(0, 0, 0), truncati
     c.hash_slots = hash_slots
     c.max_probe = max_probe
     c.payload = GSDF_PAYLOAD_F16 if fp16 else GSDF_PAYLOAD_F32
-    c.max_touched_blocks = max(1, hash_slots // 4) if max_touched_blocks is None else max_touched_blocks
+    c.max_touched_blocks = max(1, hash_slots // 4) if max_touched_blocks is None else max_touched_blocks  # power of 2
     return c
 
 
