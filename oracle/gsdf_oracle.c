@@ -610,3 +610,193 @@ size_t orc_extract(const orc_map* map, orc_voxel_out* out, size_t cap) {
     qsort(out, k, sizeof(orc_voxel_out), orc_cmp_voxel);
     return n;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* photometric + geometric voxel energy (Sec. 4.2) and its gradient                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* surface point p = v - psi ghat of voxel j (Eq. grad_sdf_project); 0 if g = 0 */
+static int orc_surface_point(const int32_t* m, const double* psi, const double* g, int64_t j, double vs,
+                             double p[3], double gh[3], double* gn) {
+    const double* gj = g + 3 * j;
+    double n = sqrt(gj[0] * gj[0] + gj[1] * gj[1] + gj[2] * gj[2]);
+    if (!(n > 0.0)) return 0;
+    for (int k = 0; k < 3; ++k) {
+        gh[k] = gj[k] / n;
+        p[k] = vs * (double)m[3 * j + k] - psi[j] * gh[k];
+    }
+    *gn = n;
+    return 1;
+}
+
+/* camera coordinates x = R^T (p - t) of a world point for pose T (camera -> world) */
+static void orc_to_camera(const double* T, const double p[3], double x[3]) {
+    const double d[3] = {p[0] - T[3], p[1] - T[7], p[2] - T[11]};
+    for (int i = 0; i < 3; ++i) x[i] = T[0 * 4 + i] * d[0] + T[1 * 4 + i] * d[1] + T[2 * 4 + i] * d[2];
+}
+
+void orc_visibility(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int n_frames,
+                    const orc_intrinsics* K, const double* poses, const float* const* depth, uint8_t* nu) {
+    const double vs = (double)voxel_size;
+    for (int i = 0; i < n_frames; ++i) {
+        const double* T = poses + 16 * i;
+        for (int64_t j = 0; j < n; ++j) {
+            uint8_t vis = 0;
+            double p[3], gh[3], gn, x[3];
+            if (orc_surface_point(m, psi, g, j, vs, p, gh, &gn)) {
+                int surface = 1;
+                for (int k = 0; k < 3; ++k) surface &= fabs(psi[j] * gh[k]) <= 0.5 * vs;
+                orc_to_camera(T, p, x);
+                if (surface && x[2] > 0.0) {
+                    const double u = K->fx * x[0] / x[2] + K->cx, v = K->fy * x[1] / x[2] + K->cy;
+                    if (u >= 1.0 && u <= K->width - 2.0 && v >= 1.0 && v <= K->height - 2.0) {
+                        const int iu = (int)floor(u + 0.5), iv = (int)floor(v + 0.5);
+                        const float D = depth[i][(size_t)iv * K->width + iu];
+                        if (orc_depth_ok(D, K->depth_max) && fabs(x[2] - (double)D) <= vs) vis = 1;
+                    }
+                }
+            }
+            nu[(size_t)i * n + j] = vis;
+        }
+    }
+}
+
+typedef struct {
+    int32_t m[3];
+    int64_t idx;
+} orc_key_index;
+
+static int orc_cmp_key(const void* pa, const void* pb) {
+    const orc_key_index* a = (const orc_key_index*)pa;
+    const orc_key_index* b = (const orc_key_index*)pb;
+    for (int k = 0; k < 3; ++k) {
+        if (a->m[k] < b->m[k]) return -1;
+        if (a->m[k] > b->m[k]) return 1;
+    }
+    return 0;
+}
+
+int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, const double* rho, float voxel_size,
+               int n_frames, const orc_intrinsics* K, const double* poses, const float* const* rgb,
+               const float* const* depth, const uint8_t* nu, double lambda_geo, double E[3], double* dpsi,
+               double* dg, double* drho, double* dxi) {
+    const double vs = (double)voxel_size;
+    const int grad = dpsi != NULL;
+    const int Wd = K->width, Hd = K->height;
+    if (grad) {
+        for (int64_t j = 0; j < n; ++j) {
+            dpsi[j] = 0.0;
+            for (int k = 0; k < 3; ++k) dg[3 * j + k] = drho[3 * j + k] = 0.0;
+        }
+        for (int k = 0; k < 6 * n_frames; ++k) dxi[k] = 0.0;
+    }
+    double Ep = 0.0, Eg = 0.0;
+    /* photometric term, Eqs. (rgb_cost), (intensity_proj) with an explicit colour rho_j */
+    for (int i = 0; i < n_frames; ++i) {
+        const double* T = poses + 16 * i;
+        const float* img = rgb[i];
+        for (int64_t j = 0; j < n; ++j) {
+            if (!nu[(size_t)i * n + j]) continue;
+            double p[3], gh[3], gn, x[3];
+            if (!orc_surface_point(m, psi, g, j, vs, p, gh, &gn)) continue;
+            orc_to_camera(T, p, x);
+            const double z = x[2];
+            const double u = K->fx * x[0] / z + K->cx, v = K->fy * x[1] / z + K->cy;
+            int x0 = (int)floor(u), y0 = (int)floor(v);
+            if (x0 < 0) x0 = 0;
+            if (x0 > Wd - 2) x0 = Wd - 2;
+            if (y0 < 0) y0 = 0;
+            if (y0 > Hd - 2) y0 = Hd - 2;
+            const double a = u - x0, b = v - y0;
+            double dEdu = 0.0, dEdv = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double I00 = img[((size_t)y0 * Wd + x0) * 3 + c], I01 = img[((size_t)y0 * Wd + x0 + 1) * 3 + c];
+                const double I10 = img[((size_t)(y0 + 1) * Wd + x0) * 3 + c];
+                const double I11 = img[((size_t)(y0 + 1) * Wd + x0 + 1) * 3 + c];
+                const double I = (1 - a) * (1 - b) * I00 + a * (1 - b) * I01 + (1 - a) * b * I10 + a * b * I11;
+                const double r = I - rho[3 * j + c];
+                Ep += r * r;
+                if (grad) {
+                    drho[3 * j + c] -= 2.0 * r;
+                    dEdu += 2.0 * r * ((1 - b) * (I01 - I00) + b * (I11 - I10));
+                    dEdv += 2.0 * r * ((1 - a) * (I10 - I00) + a * (I11 - I01));
+                }
+            }
+            if (!grad) continue;
+            /* chain rule: (u, v) <- x (pinhole) <- p (x = R^T (p - t)) <- (psi, g) and the pose */
+            const double dx[3] = {dEdu * K->fx / z, dEdv * K->fy / z,
+                                  -(dEdu * K->fx * x[0] + dEdv * K->fy * x[1]) / (z * z)};
+            double q[3];  /* dE/dp = R dE/dx */
+            for (int r_ = 0; r_ < 3; ++r_) q[r_] = T[4 * r_ + 0] * dx[0] + T[4 * r_ + 1] * dx[1] + T[4 * r_ + 2] * dx[2];
+            const double qg = q[0] * gh[0] + q[1] * gh[1] + q[2] * gh[2];
+            dpsi[j] += -qg;                                            /* dp/dpsi = -ghat */
+            for (int k = 0; k < 3; ++k) dg[3 * j + k] += -psi[j] * (q[k] - gh[k] * qg) / gn;  /* dghat/dg */
+            /* left perturbation of the pose: dx/domega = R^T [p]x, dx/dupsilon = -R^T */
+            double* dx_i = dxi + 6 * i;
+            dx_i[0] += q[1] * p[2] - q[2] * p[1];
+            dx_i[1] += q[2] * p[0] - q[0] * p[2];
+            dx_i[2] += q[0] * p[1] - q[1] * p[0];
+            dx_i[3] -= q[0];
+            dx_i[4] -= q[1];
+            dx_i[5] -= q[2];
+        }
+    }
+    /* geometric term, Eq. (tracking) with Eq. (taylor), squared residuals, every keyframe */
+    orc_key_index* keys = (orc_key_index*)malloc(sizeof(orc_key_index) * (size_t)(n > 0 ? n : 1));
+    if (!keys) return -1;
+    for (int64_t j = 0; j < n; ++j) {
+        keys[j].m[0] = m[3 * j];
+        keys[j].m[1] = m[3 * j + 1];
+        keys[j].m[2] = m[3 * j + 2];
+        keys[j].idx = j;
+    }
+    qsort(keys, (size_t)n, sizeof(orc_key_index), orc_cmp_key);
+    orc_recip rc = orc_recips(K, voxel_size);
+    for (int i = 0; i < n_frames && lambda_geo != 0.0; ++i) {
+        orc_pose32 q32;
+        orc_round_pose(poses + 16 * i, &q32);
+        for (int v = 0; v < Hd; ++v) {
+            for (int u = 0; u < Wd; ++u) {
+                const float D = depth[i][(size_t)v * Wd + u];
+                if (!orc_depth_ok(D, K->depth_max)) continue;
+                float dw[3], Pf[3];
+                orc_key_index key;
+                orc_ray_world(K, &rc, q32.R, u, v, dw);
+                orc_ray_point(dw, q32.t, D, Pf);
+                orc_round_voxel(Pf, rc.inv_vs, key.m);
+                const orc_key_index* hit = (const orc_key_index*)bsearch(&key, keys, (size_t)n, sizeof(orc_key_index),
+                                                                         orc_cmp_key);
+                if (!hit) continue;
+                const int64_t j = hit->idx;
+                const double* gj = g + 3 * j;
+                const double gn = sqrt(gj[0] * gj[0] + gj[1] * gj[1] + gj[2] * gj[2]);
+                if (!(gn > 0.0)) continue;
+                const double P[3] = {Pf[0], Pf[1], Pf[2]};
+                double gh[3], d[3], r = psi[j];
+                for (int k = 0; k < 3; ++k) {
+                    gh[k] = gj[k] / gn;
+                    d[k] = P[k] - vs * (double)key.m[k];
+                    r += gh[k] * d[k];
+                }
+                Eg += r * r;
+                if (!grad) continue;
+                const double s = 2.0 * lambda_geo * r;
+                dpsi[j] += s;
+                const double gd = gh[0] * d[0] + gh[1] * d[1] + gh[2] * d[2];
+                for (int k = 0; k < 3; ++k) dg[3 * j + k] += s * (d[k] - gh[k] * gd) / gn;
+                double* dx_i = dxi + 6 * i;
+                dx_i[0] += s * (P[1] * gh[2] - P[2] * gh[1]);
+                dx_i[1] += s * (P[2] * gh[0] - P[0] * gh[2]);
+                dx_i[2] += s * (P[0] * gh[1] - P[1] * gh[0]);
+                dx_i[3] += s * gh[0];
+                dx_i[4] += s * gh[1];
+                dx_i[5] += s * gh[2];
+            }
+        }
+    }
+    free(keys);
+    E[0] = Ep + lambda_geo * Eg;
+    E[1] = Ep;
+    E[2] = Eg;
+    return 0;
+}

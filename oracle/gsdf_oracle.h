@@ -101,6 +101,32 @@ size_t orc_extract(const orc_map* map, orc_voxel_out* out, size_t cap);
 /* block coordinate (floor division by 8) and local index of a voxel coordinate */
 void orc_block_of(const int32_t m[3], int32_t b[3], int32_t local[3]);
 
+/* ---------------------------------------------------------------------------------------------
+ * Photometric + geometric voxel energy (Sec. 4.2, Eqs. rgb_cost, intensity_proj, mean_color,
+ * variance; Eq. tracking) and its gradient, in FP64.
+ *   surface point of voxel j:  p_j = v_j - psi_j ghat_j,  ghat = g / |g|   (Eq. grad_sdf_project)
+ *   photometric:  E_p = sum_{i,j,c} nu_ij (I_i^c(pi(R_i^T (p_j - t_i))) - rho_j^c)^2, bilinear I
+ *   geometric:    E_g = sum_i sum_k r_ik^2, r = psi_m + ghat_m . (P - v_m) at the nearest voxel m
+ *                 of the back-projected pixel P (the FP32 index path), pixels without a voxel,
+ *                 with W = 0 (not in the list) or g = 0 skipped
+ *   E = E_p + lambda E_g.  Gradients: dE/dpsi, dE/dg (3n), dE/drho (3n) and, per keyframe, dE/dxi
+ *   for a left perturbation T_i <- exp(xi^) T_i, xi = (omega, upsilon).
+ * Voxels are given as a list (m[3n] integer coordinates, psi[n], g[3n], rho[3n]); images are
+ * H x W x 3 FP32 (rgb) and H x W FP32 (depth), one per keyframe, all with intrinsics K.
+ * ------------------------------------------------------------------------------------------- */
+
+/* visibility nu[i * n + j] in {0, 1}: voxel j is a surface voxel (|psi_j ghat_j| <= v_s / 2 per
+ * component, Sec. 4.3), its surface point projects into keyframe i with a one-pixel margin, in
+ * front of the camera, and within v_s of the keyframe's depth at the nearest pixel */
+void orc_visibility(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int n_frames,
+                    const orc_intrinsics* K, const double* poses, const float* const* depth, uint8_t* nu);
+
+/* energy E[3] = (E, E_p, E_g) and, if dpsi != NULL, the full gradient */
+int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, const double* rho, float voxel_size,
+               int n_frames, const orc_intrinsics* K, const double* poses, const float* const* rgb,
+               const float* const* depth, const uint8_t* nu, double lambda_geo, double E[3], double* dpsi,
+               double* dg, double* drho, double* dxi);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,12 @@ def lib():
         L.orc_extract.restype = C.c_size_t
         L.orc_extract.argtypes = [C.c_void_p, P(VoxelOut), C.c_size_t]
         L.orc_block_of.argtypes = [P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+        L.orc_visibility.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), C.c_float, C.c_int,
+                                     P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(C.c_uint8)]
+        L.orc_energy.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double), C.c_float,
+                                 C.c_int, P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(P(C.c_float)),
+                                 P(C.c_uint8), C.c_double, P(C.c_double), P(C.c_double), P(C.c_double),
+                                 P(C.c_double), P(C.c_double)]
         _lib = L
     return _lib
 
@@ -232,3 +238,52 @@ def block_of(m):
     loc = np.zeros(3, np.int32)
     lib().orc_block_of(_ptr(ma, C.c_int32), _ptr(b, C.c_int32), _ptr(loc, C.c_int32))
     return b, loc
+
+
+def _frames_ptrs(frames):
+    arrs = [np.ascontiguousarray(f, np.float32) for f in frames]
+    ptrs = (C.POINTER(C.c_float) * len(arrs))(*[_ptr(a, C.c_float) for a in arrs])
+    return arrs, ptrs
+
+
+def visibility(m, psi, g, voxel_size, cam, poses, depths):
+    """nu (F, n) uint8 of the photometric energy (surface voxel, inside with a 1 px margin, depth test)."""
+    m = np.ascontiguousarray(m, np.int32)
+    psi = np.ascontiguousarray(psi, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    n, F = len(psi), len(poses)
+    P = np.ascontiguousarray(np.stack([np.asarray(T, np.float64).reshape(16) for T in poses]))
+    keep, dptr = _frames_ptrs(depths)
+    nu = np.zeros((F, n), np.uint8)
+    K = intrinsics(cam)
+    lib().orc_visibility(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), _ptr(g, C.c_double), voxel_size, F,
+                         C.byref(K), _ptr(P, C.c_double), dptr, _ptr(nu, C.c_uint8))
+    return nu
+
+
+def energy(m, psi, g, rho, voxel_size, cam, poses, rgbs, depths, nu, lambda_geo, grad=True):
+    """(E, E_p, E_g) and, if grad, (dpsi, dg (n,3), drho (n,3), dxi (F,6)) of the voxel energy."""
+    m = np.ascontiguousarray(m, np.int32)
+    psi = np.ascontiguousarray(psi, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    nu = np.ascontiguousarray(nu, np.uint8)
+    n, F = len(psi), len(poses)
+    P = np.ascontiguousarray(np.stack([np.asarray(T, np.float64).reshape(16) for T in poses]))
+    keep_r, rptr = _frames_ptrs(rgbs)
+    keep_d, dptr = _frames_ptrs(depths)
+    E = np.zeros(3)
+    K = intrinsics(cam)
+    if grad:
+        dpsi, dg, drho, dxi = np.zeros(n), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((F, 6))
+        gp = (_ptr(dpsi, C.c_double), _ptr(dg, C.c_double), _ptr(drho, C.c_double), _ptr(dxi, C.c_double))
+    else:
+        gp = (None, None, None, None)
+    rc = lib().orc_energy(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), _ptr(g, C.c_double), _ptr(rho, C.c_double),
+                          voxel_size, F, C.byref(K), _ptr(P, C.c_double), rptr, dptr, _ptr(nu, C.c_uint8),
+                          lambda_geo, _ptr(E, C.c_double), *gp)
+    if rc != 0:
+        raise MemoryError("orc_energy failed")
+    if grad:
+        return E, dpsi, dg, drho, dxi
+    return E

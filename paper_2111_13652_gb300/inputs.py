@@ -173,12 +173,29 @@ class RoomScene:
     boxes: list  # [(lo(3,), hi(3,))]
 
     def raycast(self, o, d):
-        t = _ray_room_exit(o, d, self.lo, self.hi)
-        for c, r in self.spheres:
-            t = np.minimum(t, _ray_sphere(o, d, c, r))
-        for blo, bhi in self.boxes:
-            t = np.minimum(t, _ray_box(o, d, blo, bhi))
-        return t
+        return self.raycast_id(o, d)[0]
+
+    def raycast_id(self, o, d):
+        """Ray parameter and surface id: 0..5 the walls (-x, +x, -y, +y, -z, +z), 6.. spheres, then boxes."""
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / d
+            t_hi = (self.hi - o) * inv
+            t_lo = (self.lo - o) * inv
+        t_exit = np.where(d > 0, t_hi, np.where(d < 0, t_lo, np.inf))
+        axis = np.argmin(t_exit, axis=1)
+        t = t_exit[np.arange(len(d)), axis]
+        sid = 2 * axis + (d[np.arange(len(d)), axis] > 0)
+        for k, (c, r) in enumerate(self.spheres):
+            ts = _ray_sphere(o, d, c, r)
+            closer = ts < t
+            t = np.where(closer, ts, t)
+            sid = np.where(closer, 6 + k, sid)
+        for k, (blo, bhi) in enumerate(self.boxes):
+            tb = _ray_box(o, d, blo, bhi)
+            closer = tb < t
+            t = np.where(closer, tb, t)
+            sid = np.where(closer, 6 + len(self.spheres) + k, sid)
+        return t, sid
 
     def free_clearance(self, x):
         """Distance from point x to the nearest obstacle surface (positive in free space)."""
@@ -467,3 +484,72 @@ def batch_scenes(n_scenes: int, n_frames: int, seed: int = 5, processes: int = 1
         with cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
             return list(ex.map(functools.partial(batch_scene, n_frames=n_frames, seed=seed), range(n_scenes)))
     return [batch_scene(i, n_frames, seed) for i in range(n_scenes)]
+
+
+# --------------------------------------------------------------------------------------------
+# colour: per-surface albedo times 3-octave value noise (Lambertian-free: intensity = albedo)
+# --------------------------------------------------------------------------------------------
+
+
+def _value_noise(p: np.ndarray, seed: int, spacing: float) -> np.ndarray:
+    """Trilinearly interpolated random lattice values in [0, 1) at points p (n, 3)."""
+    q = p / spacing
+    base = np.floor(q).astype(np.int64)
+    f = q - base
+    out = np.zeros(len(p))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                c = base + np.array([dx, dy, dz])
+                h = (c[:, 0] * 73856093) ^ (c[:, 1] * 19349663) ^ (c[:, 2] * 83492791) ^ (seed * 2654435761)
+                h = (h * 0x9E3779B1) & 0xFFFFFFFF
+                val = (h % 100003) / 100003.0
+                wgt = (f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) * (f[:, 2] if dz else 1 - f[:, 2])
+                out += wgt * val
+    return out
+
+
+def surface_albedo(n_surfaces: int, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed + 31337).uniform(0.2, 0.9, size=(n_surfaces, 3))
+
+
+def render_rgbd(scene: RoomScene, cam: Camera, T_wc: np.ndarray, seed: int):
+    """FP64 ray cast returning (depth (H, W) FP32, rgb (H, W, 3) FP32): colour = per-surface albedo
+    (uniform in [0.2, 0.9] per channel) times 0.6 + 0.4 * 3-octave value noise of the hit point."""
+    dc = cam.ray_dirs_cam()
+    d = dc @ T_wc[:3, :3].T
+    o = T_wc[:3, 3]
+    t, sid = scene.raycast_id(o, d)
+    hit = np.isfinite(t)
+    depth = np.where(hit, t, 0.0)
+    pts = o + d * np.where(hit, t, 0.0)[:, None]
+    noise = (_value_noise(pts, seed, 0.2) + 0.5 * _value_noise(pts, seed + 1, 0.1) +
+             0.25 * _value_noise(pts, seed + 2, 0.05)) / 1.75
+    alb = surface_albedo(6 + len(scene.spheres) + len(scene.boxes), seed)[sid]
+    rgb = alb * (0.6 + 0.4 * noise)[:, None]
+    rgb = np.where(hit[:, None], rgb, 0.0)
+    return (depth.reshape(cam.height, cam.width).astype(np.float32),
+            rgb.reshape(cam.height, cam.width, 3).astype(np.float32))
+
+
+@dataclasses.dataclass
+class KeyframeSet:
+    cam: Camera
+    scene: RoomScene
+    poses: list
+    depths: np.ndarray  # (F, H, W)
+    rgbs: np.ndarray  # (F, H, W, 3)
+    voxel_size: float
+
+
+def keyframes(seed: int = 2, n_keyframes: int = 10, stride: int = 10, cam: Camera = KINECT_640,
+              voxel_size: float = 0.01) -> KeyframeSet:
+    """RGB-D keyframes (every `stride`-th frame of the room trajectory), noise-free depth."""
+    scene = make_room(seed)
+    poses_all = room_trajectory(scene, n_keyframes * stride, seed)
+    poses = poses_all[::stride][:n_keyframes]
+    depths = np.empty((n_keyframes, cam.height, cam.width), np.float32)
+    rgbs = np.empty((n_keyframes, cam.height, cam.width, 3), np.float32)
+    for i, T in enumerate(poses):
+        depths[i], rgbs[i] = render_rgbd(scene, cam, T, seed)
+    return KeyframeSet(cam, scene, poses, depths, rgbs, voxel_size)
