@@ -635,25 +635,60 @@ static void orc_to_camera(const double* T, const double p[3], double x[3]) {
     for (int i = 0; i < 3; ++i) x[i] = T[0 * 4 + i] * d[0] + T[1 * 4 + i] * d[1] + T[2 * 4 + i] * d[2];
 }
 
+/* FP32 index path of the energy's pixel decisions for voxel j in a keyframe: the surface point,
+ * its camera coordinates and its projection, every operation rounded to FP32 in the order
+ * written, from psi and g rounded to FP32 and the pose rounded once (orc_round_pose):
+ *   n2 = (g0 g0 + g1 g1) + g2 g2,  ghat_k = g_k / sqrt(n2),  s_k = psi ghat_k,  p_k = v_s m_k - s_k
+ *   d = p - t,  x_i = (R_0i d_0 + R_1i d_1) + R_2i d_2,  u = (f_x x_0) / x_2 + c_x,  v likewise.
+ * Returns 0 if g rounds to zero or the point is not in front of the camera (x_2 <= 0). */
+typedef struct {
+    float s[3], x[3], u, v;
+} orc_proj32;
+
+static int orc_project32(const int32_t* m, const double* psi, const double* g, int64_t j, float vs,
+                         const orc_pose32* q, const orc_intrinsics* K, orc_proj32* o) {
+    const float gj[3] = {(float)g[3 * j], (float)g[3 * j + 1], (float)g[3 * j + 2]};
+    const float ps = (float)psi[j];
+    float n2 = gj[0] * gj[0];
+    n2 = n2 + gj[1] * gj[1];
+    n2 = n2 + gj[2] * gj[2];
+    if (!(n2 > 0.0f)) return 0;
+    const float nr = sqrtf(n2);
+    float d[3];
+    for (int k = 0; k < 3; ++k) {
+        const float gh = gj[k] / nr;
+        o->s[k] = ps * gh;
+        const float v = vs * (float)m[3 * j + k];
+        const float p = v - o->s[k];
+        d[k] = p - q->t[k];
+    }
+    for (int i = 0; i < 3; ++i) {
+        float a = q->R[0 * 3 + i] * d[0];
+        a = a + q->R[1 * 3 + i] * d[1];
+        o->x[i] = a + q->R[2 * 3 + i] * d[2];
+    }
+    if (!(o->x[2] > 0.0f)) return 0;
+    o->u = (K->fx * o->x[0]) / o->x[2] + K->cx;
+    o->v = (K->fy * o->x[1]) / o->x[2] + K->cy;
+    return 1;
+}
+
 void orc_visibility(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int n_frames,
                     const orc_intrinsics* K, const double* poses, const float* const* depth, uint8_t* nu) {
-    const double vs = (double)voxel_size;
+    const float vs = voxel_size, half = 0.5f * voxel_size;
     for (int i = 0; i < n_frames; ++i) {
-        const double* T = poses + 16 * i;
+        orc_pose32 q;
+        orc_round_pose(poses + 16 * i, &q);
         for (int64_t j = 0; j < n; ++j) {
             uint8_t vis = 0;
-            double p[3], gh[3], gn, x[3];
-            if (orc_surface_point(m, psi, g, j, vs, p, gh, &gn)) {
-                int surface = 1;
-                for (int k = 0; k < 3; ++k) surface &= fabs(psi[j] * gh[k]) <= 0.5 * vs;
-                orc_to_camera(T, p, x);
-                if (surface && x[2] > 0.0) {
-                    const double u = K->fx * x[0] / x[2] + K->cx, v = K->fy * x[1] / x[2] + K->cy;
-                    if (u >= 1.0 && u <= K->width - 2.0 && v >= 1.0 && v <= K->height - 2.0) {
-                        const int iu = (int)floor(u + 0.5), iv = (int)floor(v + 0.5);
-                        const float D = depth[i][(size_t)iv * K->width + iu];
-                        if (orc_depth_ok(D, K->depth_max) && fabs(x[2] - (double)D) <= vs) vis = 1;
-                    }
+            orc_proj32 o;
+            if (orc_project32(m, psi, g, j, vs, &q, K, &o)) {
+                const int surface = fabsf(o.s[0]) <= half && fabsf(o.s[1]) <= half && fabsf(o.s[2]) <= half;
+                if (surface && o.u >= 1.0f && o.u <= (float)(K->width - 2) && o.v >= 1.0f &&
+                    o.v <= (float)(K->height - 2)) {
+                    const int iu = (int)floorf(o.u + 0.5f), iv = (int)floorf(o.v + 0.5f);
+                    const float D = depth[i][(size_t)iv * K->width + iu];
+                    if (orc_depth_ok(D, K->depth_max) && fabsf(o.x[2] - D) <= vs) vis = 1;
                 }
             }
             nu[(size_t)i * n + j] = vis;
@@ -679,7 +714,7 @@ static int orc_cmp_key(const void* pa, const void* pb) {
 int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, const double* rho, float voxel_size,
                int n_frames, const orc_intrinsics* K, const double* poses, const float* const* rgb,
                const float* const* depth, const uint8_t* nu, double lambda_geo, double E[3], double* dpsi,
-               double* dg, double* drho, double* dxi) {
+               double* dg, double* drho, double* dxi, double* dT) {
     const double vs = (double)voxel_size;
     const int grad = dpsi != NULL;
     const int Wd = K->width, Hd = K->height;
@@ -689,24 +724,32 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
             for (int k = 0; k < 3; ++k) dg[3 * j + k] = drho[3 * j + k] = 0.0;
         }
         for (int k = 0; k < 6 * n_frames; ++k) dxi[k] = 0.0;
+        if (dT)
+            for (int k = 0; k < 16 * n_frames; ++k) dT[k] = 0.0;
     }
     double Ep = 0.0, Eg = 0.0;
     /* photometric term, Eqs. (rgb_cost), (intensity_proj) with an explicit colour rho_j */
     for (int i = 0; i < n_frames; ++i) {
         const double* T = poses + 16 * i;
         const float* img = rgb[i];
+        orc_pose32 q32;
+        orc_round_pose(T, &q32);
         for (int64_t j = 0; j < n; ++j) {
             if (!nu[(size_t)i * n + j]) continue;
+            /* decisions on the FP32 index path: the pair counts while its point projects into the
+             * image at the evaluated pose; the bilinear cell is (floor u, floor v), kept inside */
+            orc_proj32 o;
+            if (!orc_project32(m, psi, g, j, voxel_size, &q32, K, &o)) continue;
+            if (!(o.u >= 0.0f && o.u <= (float)(Wd - 1) && o.v >= 0.0f && o.v <= (float)(Hd - 1))) continue;
+            int x0 = (int)floorf(o.u), y0 = (int)floorf(o.v);
+            if (x0 > Wd - 2) x0 = Wd - 2;
+            if (y0 > Hd - 2) y0 = Hd - 2;
+            /* values in FP64 */
             double p[3], gh[3], gn, x[3];
             if (!orc_surface_point(m, psi, g, j, vs, p, gh, &gn)) continue;
             orc_to_camera(T, p, x);
             const double z = x[2];
             const double u = K->fx * x[0] / z + K->cx, v = K->fy * x[1] / z + K->cy;
-            int x0 = (int)floor(u), y0 = (int)floor(v);
-            if (x0 < 0) x0 = 0;
-            if (x0 > Wd - 2) x0 = Wd - 2;
-            if (y0 < 0) y0 = 0;
-            if (y0 > Hd - 2) y0 = Hd - 2;
             const double a = u - x0, b = v - y0;
             double dEdu = 0.0, dEdv = 0.0;
             for (int c = 0; c < 3; ++c) {
@@ -739,6 +782,14 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
             dx_i[3] -= q[0];
             dx_i[4] -= q[1];
             dx_i[5] -= q[2];
+            if (dT) { /* entries of T: dE/dR_ab = (p - t)_a dE/dx_b, dE/dt = -R dE/dx */
+                double* G = dT + 16 * i;
+                for (int a_ = 0; a_ < 3; ++a_) {
+                    const double pa = p[a_] - T[4 * a_ + 3];
+                    for (int b_ = 0; b_ < 3; ++b_) G[4 * a_ + b_] += pa * dx[b_];
+                    G[4 * a_ + 3] -= q[a_];
+                }
+            }
         }
     }
     /* geometric term, Eq. (tracking) with Eq. (taylor), squared residuals, every keyframe */
@@ -791,6 +842,14 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
                 dx_i[3] += s * gh[0];
                 dx_i[4] += s * gh[1];
                 dx_i[5] += s * gh[2];
+                if (dT) { /* P = R p_c + t with the camera point p_c = D ((u - c_x)/f_x, (v - c_y)/f_y, 1) */
+                    const double pc[3] = {D * ((u - (double)K->cx) / K->fx), D * ((v - (double)K->cy) / K->fy), D};
+                    double* G = dT + 16 * i;
+                    for (int a_ = 0; a_ < 3; ++a_) {
+                        for (int b_ = 0; b_ < 3; ++b_) G[4 * a_ + b_] += s * gh[a_] * pc[b_];
+                        G[4 * a_ + 3] += s * gh[a_];
+                    }
+                }
             }
         }
     }

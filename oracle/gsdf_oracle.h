@@ -115,17 +115,24 @@ void orc_block_of(const int32_t m[3], int32_t b[3], int32_t local[3]);
  * H x W x 3 FP32 (rgb) and H x W FP32 (depth), one per keyframe, all with intrinsics K.
  * ------------------------------------------------------------------------------------------- */
 
-/* visibility nu[i * n + j] in {0, 1}: voxel j is a surface voxel (|psi_j ghat_j| <= v_s / 2 per
+/* Discrete decisions (visibility, the photometric pair's bilinear cell) are taken on an FP32
+ * index path from psi and g rounded to FP32 and the pose rounded to FP32 (order of operations in
+ * the source); values stay FP64.
+ * visibility nu[i * n + j] in {0, 1}: voxel j is a surface voxel (|psi_j ghat_j| <= v_s / 2 per
  * component, Sec. 4.3), its surface point projects into keyframe i with a one-pixel margin, in
- * front of the camera, and within v_s of the keyframe's depth at the nearest pixel */
+ * front of the camera, and within v_s of the keyframe's depth at the nearest pixel.
+ * In the energy a pair with nu_ij = 1 counts while its point projects into the image
+ * (0 <= u <= W - 1, 0 <= v <= H - 1, in front) at the evaluated pose. */
 void orc_visibility(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int n_frames,
                     const orc_intrinsics* K, const double* poses, const float* const* depth, uint8_t* nu);
 
-/* energy E[3] = (E, E_p, E_g) and, if dpsi != NULL, the full gradient */
+/* energy E[3] = (E, E_p, E_g) and, if dpsi != NULL, the full gradient; dT (may be NULL) gets, per
+ * keyframe, dE/dT_ab for the 12 entries of T = [R t] as free variables (row-major 4 x 4, last row
+ * zero), the gradient an autograd caller chains through */
 int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, const double* rho, float voxel_size,
                int n_frames, const orc_intrinsics* K, const double* poses, const float* const* rgb,
                const float* const* depth, const uint8_t* nu, double lambda_geo, double E[3], double* dpsi,
-               double* dg, double* drho, double* dxi);
+               double* dg, double* drho, double* dxi, double* dT);
 
 #ifdef __cplusplus
 }

@@ -88,7 +88,7 @@ def lib():
         L.orc_energy.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double), C.c_float,
                                  C.c_int, P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(P(C.c_float)),
                                  P(C.c_uint8), C.c_double, P(C.c_double), P(C.c_double), P(C.c_double),
-                                 P(C.c_double), P(C.c_double)]
+                                 P(C.c_double), P(C.c_double), P(C.c_double)]
         _lib = L
     return _lib
 
@@ -262,7 +262,10 @@ def visibility(m, psi, g, voxel_size, cam, poses, depths):
 
 
 def energy(m, psi, g, rho, voxel_size, cam, poses, rgbs, depths, nu, lambda_geo, grad=True):
-    """(E, E_p, E_g) and, if grad, (dpsi, dg (n,3), drho (n,3), dxi (F,6)) of the voxel energy."""
+    """(E, E_p, E_g) and, if grad, (dpsi, dg (n,3), drho (n,3), dxi (F,6), dT (F,4,4)) of the voxel energy.
+
+    dxi is the gradient for a left perturbation T <- exp(xi^) T, dT the gradient with respect to
+    the entries of T = [R t] taken as free variables."""
     m = np.ascontiguousarray(m, np.int32)
     psi = np.ascontiguousarray(psi, np.float64)
     g = np.ascontiguousarray(g, np.float64)
@@ -276,14 +279,16 @@ def energy(m, psi, g, rho, voxel_size, cam, poses, rgbs, depths, nu, lambda_geo,
     K = intrinsics(cam)
     if grad:
         dpsi, dg, drho, dxi = np.zeros(n), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((F, 6))
-        gp = (_ptr(dpsi, C.c_double), _ptr(dg, C.c_double), _ptr(drho, C.c_double), _ptr(dxi, C.c_double))
+        dT = np.zeros((F, 4, 4))
+        gp = (_ptr(dpsi, C.c_double), _ptr(dg, C.c_double), _ptr(drho, C.c_double), _ptr(dxi, C.c_double),
+              _ptr(dT, C.c_double))
     else:
-        gp = (None, None, None, None)
+        gp = (None, None, None, None, None)
     rc = lib().orc_energy(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), _ptr(g, C.c_double), _ptr(rho, C.c_double),
                           voxel_size, F, C.byref(K), _ptr(P, C.c_double), rptr, dptr, _ptr(nu, C.c_uint8),
                           lambda_geo, _ptr(E, C.c_double), *gp)
     if rc != 0:
         raise MemoryError("orc_energy failed")
     if grad:
-        return E, dpsi, dg, drho, dxi
+        return E, dpsi, dg, drho, dxi, dT
     return E

@@ -1,9 +1,14 @@
 """Pins of the oracle's photometric + geometric voxel energy (Sec. 4.2) and its gradient.
 
 * Central finite differences of the oracle's own energy: psi, g and rho entries (photometric and
-  geometric terms), and the keyframe poses under a left perturbation by scipy's matrix exponential
-  (photometric term; the geometric term is piecewise in the pose because of the FP32 voxel
-  rounding, so it is pinned by the next item instead).
+  geometric terms), the keyframe poses under a left perturbation by scipy's matrix exponential,
+  and the 12 entries of each pose matrix (both terms).  The energy is piecewise smooth in the
+  pose: the bilinear cell and the geometric term's voxel are discrete choices.  The pose
+  differences therefore run on a visibility subset whose points stay 1e-2 px away from any cell
+  boundary and on depth images whose back-projected points stay 1e-3 v_s away from any voxel
+  boundary, so that no choice changes within the step.
+* The left-perturbation gradient equals the matrix gradient contracted with the generators
+  [e_k]x T of SE(3) (two separately written formulas).
 * The geometric pose gradient against the tracking reduction, a separately written code path:
   with a Huber threshold too large to clip, b = sum J r, so dE_g/dxi = 2 b per keyframe and
   E_g = sum of the tracking energies.
@@ -38,6 +43,48 @@ def _twist(xi):
     M[:3, :3] = [[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]
     M[:3, 3] = u
     return M
+
+
+def _safe_nu(ks, ex, nu, margin=1e-2, poses=None):
+    """nu without the pairs whose projection lies within `margin` px of a bilinear cell boundary."""
+    vs = np.float64(np.float32(ks.voxel_size))
+    gh = ex["g"] / np.linalg.norm(ex["g"], axis=1, keepdims=True)
+    p = ex["m"] * vs - ex["psi"][:, None] * gh
+    out = nu.copy()
+    for i, T in enumerate(ks.poses if poses is None else poses):
+        x = (p - T[:3, 3]) @ T[:3, :3]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = ks.cam.fx * x[:, 0] / x[:, 2] + ks.cam.cx
+            v = ks.cam.fy * x[:, 1] / x[:, 2] + ks.cam.cy
+        near = lambda a: np.abs(a - np.round(a)) < margin  # noqa: E731
+        out[i] &= ~(near(u) | near(v))
+    return out
+
+
+def _safe_depths(ks, margin=1e-3, poses=None):
+    """Depth images with the pixels removed whose world point lies within margin * v_s of a voxel
+    boundary (half-integer multiple of v_s) on any axis."""
+    vs = float(np.float32(ks.voxel_size))
+    cam = ks.cam
+    uu, vv = np.meshgrid(np.arange(cam.width), np.arange(cam.height))
+    ray = np.stack([(uu - cam.cx) / cam.fx, (vv - cam.cy) / cam.fy, np.ones_like(uu, float)], -1)
+    out = []
+    for D, T in zip(ks.depths, ks.poses if poses is None else poses):
+        P = (D[..., None] * ray) @ T[:3, :3].T + T[:3, 3]
+        f = P / vs + 0.5
+        near = np.any(np.abs(f - np.round(f)) < margin, axis=-1)
+        out.append(np.where(near, 0.0, D).astype(np.float32))
+    return out
+
+
+def _generators(T):
+    """d/deps of exp(eps^) T at eps = 0 for eps = (omega, upsilon): six 4 x 4 matrices."""
+    G = []
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = 1.0
+        G.append(_twist(e) @ T)
+    return G
 
 
 def test_visibility_selects_surface_voxels_seen_by_several_frames(setup):
@@ -92,8 +139,9 @@ def test_visibility_against_the_analytic_scene(setup):
 def test_gradient_matches_finite_differences(setup):
     ks, _, ex, nu, rho = setup
     lam = 0.5
+    nu = _safe_nu(ks, ex, nu)
     args = (ks.voxel_size, ks.cam, ks.poses, ks.rgbs, ks.depths, nu, lam)
-    E, dpsi, dg, drho, dxi = O.energy(ex["m"], ex["psi"], ex["g"], rho, *args)
+    E, dpsi, dg, drho, dxi, _ = O.energy(ex["m"], ex["psi"], ex["g"], rho, *args)
     assert E[1] > 0 and E[2] > 0
     rng = np.random.default_rng(1)
     seen = np.nonzero(nu.sum(axis=0) > 0)[0]
@@ -118,12 +166,11 @@ def test_gradient_matches_finite_differences(setup):
         assert fd("g", j, k) == pytest.approx(dg[j, k], rel=1e-5, abs=noise)
         assert fd("rho", j, k) == pytest.approx(drho[j, k], rel=1e-6, abs=noise)
 
-    # photometric pose gradient under T <- expm(xi^) T.  A pose step moves every projected point;
-    # steps of 1e-8 keep them off the pixel boundaries where bilinear sampling has kinks, while
-    # the rounding of the two energies stays near 4 ulp(E) / 2h
+    # photometric pose gradient under T <- expm(xi^) T, on pairs away from the bilinear kinks
     argsp = (ks.voxel_size, ks.cam)
     hp = 1e-8
-    E0, _, _, _, dxi_p = O.energy(ex["m"], ex["psi"], ex["g"], rho, *argsp, ks.poses, ks.rgbs, ks.depths, nu, 0.0)
+    nu = _safe_nu(ks, ex, nu)
+    E0, _, _, _, dxi_p, _ = O.energy(ex["m"], ex["psi"], ex["g"], rho, *argsp, ks.poses, ks.rgbs, ks.depths, nu, 0.0)
     for i in range(len(ks.poses)):
         for k in range(6):
             e = np.zeros(6)
@@ -137,10 +184,49 @@ def test_gradient_matches_finite_differences(setup):
             assert (Ep - Em) / (2 * hp) == pytest.approx(dxi_p[i, k], rel=1e-4, abs=4 * np.spacing(E0[0]) / (2 * hp))
 
 
+def test_pose_matrix_gradient_matches_finite_differences(setup):
+    """dE/dT for the 12 entries of every keyframe pose, photometric and geometric terms together.
+
+    The geometric term is evaluated at the FP32 index-path point, so the poses are first rounded to
+    FP32 values and stepped by h = 2^-16: T +- h is then exact in FP32 and the rounded pose moves by
+    exactly +-h.  The FP32 rounding of the points themselves leaves a noise of about 1e-7 m per
+    pixel, about 2e-3 in the difference quotient."""
+    ks, _, ex, nu, rho = setup
+    poses = [np.float32(T).astype(np.float64) for T in ks.poses]
+    nu_s = _safe_nu(ks, ex, nu, margin=2e-2, poses=poses)
+    depths_s = _safe_depths(ks, margin=5e-3, poses=poses)
+    lam = 0.5
+    base = (ex["m"], ex["psi"], ex["g"], rho, ks.voxel_size, ks.cam)
+    E0, _, _, _, _, dT = O.energy(*base, poses, ks.rgbs, depths_s, nu_s, lam)
+    assert E0[1] > 0 and E0[2] > 0
+    h = 2.0**-16
+    for i in range(len(poses)):
+        for a in range(3):
+            for b in range(4):
+                vals = []
+                for sgn in (+1, -1):
+                    Ts = [T.copy() for T in poses]
+                    Ts[i][a, b] += sgn * h
+                    assert np.float32(Ts[i][a, b]) == Ts[i][a, b]
+                    vals.append(O.energy(*base, Ts, ks.rgbs, depths_s, nu_s, lam, grad=False)[0])
+                fd = (vals[0] - vals[1]) / (2 * h)
+                assert fd == pytest.approx(dT[i, a, b], rel=2e-5, abs=1e-2), (i, a, b)
+        assert np.all(dT[i, 3] == 0)
+
+
+def test_twist_gradient_is_matrix_gradient_on_the_generators(setup):
+    ks, _, ex, nu, rho = setup
+    _, _, _, _, dxi, dT = O.energy(ex["m"], ex["psi"], ex["g"], rho, ks.voxel_size, ks.cam, ks.poses, ks.rgbs,
+                                   ks.depths, nu, 0.5)
+    for i, T in enumerate(ks.poses):
+        want = np.array([np.sum(dT[i] * Gk) for Gk in _generators(T)])
+        assert np.allclose(dxi[i], want, rtol=1e-6, atol=1e-9 * np.abs(want).max())
+
+
 def test_geometric_pose_gradient_equals_tracking_reduction(setup):
     ks, m_, ex, nu, rho = setup
     none = np.zeros_like(nu)
-    E, _, _, _, dxi = O.energy(ex["m"], ex["psi"], ex["g"], rho, ks.voxel_size, ks.cam, ks.poses, ks.rgbs,
+    E, _, _, _, dxi, _ = O.energy(ex["m"], ex["psi"], ex["g"], rho, ks.voxel_size, ks.cam, ks.poses, ks.rgbs,
                                ks.depths, none, 1.0)
     E_track = 0.0
     for i, T in enumerate(ks.poses):
@@ -157,11 +243,11 @@ def test_mean_colour_minimises_and_variance_decomposition(setup):
     args = (ks.voxel_size, ks.cam, ks.poses, ks.rgbs, ks.depths, nu, 0.0)
     N = nu.sum(axis=0).astype(np.float64)
     zero = np.zeros((len(N), 3))
-    _, _, _, d0, _ = O.energy(ex["m"], ex["psi"], ex["g"], zero, *args)
+    _, _, _, d0, _, _ = O.energy(ex["m"], ex["psi"], ex["g"], zero, *args)
     seen = N > 0
     rho_star = np.zeros_like(zero)
     rho_star[seen] = -d0[seen] / (2 * N[seen, None])  # Eq. (mean_color)
-    E_star, _, _, d_star, _ = O.energy(ex["m"], ex["psi"], ex["g"], rho_star, *args)
+    E_star, _, _, d_star, _, _ = O.energy(ex["m"], ex["psi"], ex["g"], rho_star, *args)
     assert np.max(np.abs(d_star)) < 1e-10
     rng = np.random.default_rng(3)
     delta = rng.normal(size=zero.shape) * 0.05
