@@ -289,6 +289,71 @@ gsdf_status gsdf_batch_integrate(gsdf_batch* b);
  * Synchronous.  Optional outputs receive the choice. */
 gsdf_status gsdf_batch_autotune(gsdf_batch* b, int32_t* tile_px_out, int32_t* ctas_per_sm_out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Photometric + geometric voxel energy and its adjoint (Sec. 4.2, Eqs. rgb_cost, intensity_proj,
+ * mean_color, variance; Eq. tracking with Eq. taylor), over an explicit list of n voxels.
+ *   voxel j:    integer coordinate m_j, psi_j, g_j, colour rho_j (RGB); surface point
+ *               p_j = v_s m_j - psi_j ghat_j, ghat = g / |g| (Eq. grad_sdf_project);
+ *   keyframe i: pose T_i (camera -> world), RGB image I_i and depth image D_i, shared intrinsics;
+ *   E   = E_p + lambda E_g,
+ *   E_p = sum_{i,j,c} nu_ij (I_i^c(pi(R_i^T (p_j - t_i))) - rho_j^c)^2, I sampled bilinearly
+ *         (Eq. rgb_cost with an explicit per-voxel colour rho; at rho = the mean colour of
+ *         Eq. mean_color, E_p = sum_j N_j Var_j, Eq. variance);
+ *   E_g = sum_i sum_pixels r^2, r = psi_m + ghat_m . (P - v_s m), P the back-projected pixel at
+ *         T_i and m its nearest voxel (exactly the pixel path of gsdf_track_step), pixels whose
+ *         voxel is not in the list or has g = 0 skipped.
+ * Discrete decisions are taken on an FP32 index path with a fixed order of operations (psi, g
+ * as given in FP32, T_i rounded once to FP32):
+ *   n2 = (g0 g0 + g1 g1) + g2 g2, ghat_k = g_k / sqrt(n2), s_k = psi ghat_k, p_k = v_s m_k - s_k,
+ *   d = p - t, x_i = (R_0i d_0 + R_1i d_1) + R_2i d_2, u = (f_x x_0) / x_2 + c_x, v likewise.
+ * Visibility nu_ij = 1 iff n2 > 0, |s_k| <= v_s / 2 for every k (surface voxel, Sec. 4.3),
+ * x_2 > 0, 1 <= u <= W - 2, 1 <= v <= H - 2, and at the nearest pixel (floor(u + 1/2),
+ * floor(v + 1/2)) the depth D is valid and |x_2 - D| <= v_s.  In the energy a pair with
+ * nu_ij = 1 counts while, at the evaluated pose, n2 > 0, x_2 > 0, 0 <= u <= W - 1 and
+ * 0 <= v <= H - 1; its bilinear cell is (min(floor u, W - 2), min(floor v, H - 2)).
+ * Per-pixel lookups are recomputed by every evaluation; nothing per pixel is stored.
+ * Arithmetic: FP32 per voxel and per pixel, FP64 accumulation of the energies and pose terms.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct gsdf_energy gsdf_energy;
+
+/* Build an energy over n_voxels voxels (0 allowed) and n_frames keyframes (1..64):
+ *   m_dev      3 n int32 (device), xyz per voxel, unique, each coordinate in [-2^23, 2^23);
+ *   rgb_dev    n_frames x H x W x 3 FP32 (device), keyframe colours, row-major;
+ *   depth_dev  n_frames x H x W FP32 (device), keyframe depths (as for gsdf_integrate);
+ *   K          intrinsics shared by the keyframes, W, H >= 2.
+ * The library copies m, rgb and depth (the caller's buffers may be freed afterwards) and builds
+ * an index of the voxels by 8^3 block (a hash of block keys and a voxel table per block).  A
+ * repeated or out-of-range coordinate returns GSDF_ERR_INVALID_ARG.  Synchronous on cuda_stream,
+ * which later calls use.  Device memory: about 4 n (F + 8) bytes plus 2 KB per block and
+ * 20 F H W bytes for the images. */
+gsdf_status gsdf_energy_create(int64_t n_voxels, const int32_t* m_dev, float voxel_size, int32_t n_frames,
+                               const gsdf_intrinsics* K, const float* rgb_dev, const float* depth_dev,
+                               void* cuda_stream, gsdf_energy** out);
+gsdf_status gsdf_energy_destroy(gsdf_energy* e);
+gsdf_status gsdf_energy_set_stream(gsdf_energy* e, void* cuda_stream);
+
+/* The visibility defined above at the poses T_dev (device, n_frames x 16 FP64) for psi_dev (n FP32)
+ * and g_dev (3 n FP32), as a voxel-major bit set: nu_dev (device) holds ceil(n_frames / 32)
+ * uint32 words per voxel, word k of voxel j at nu_dev[j * ceil(n_frames / 32) + k], and bit
+ * (i mod 32) of word i / 32 is nu_ij. */
+gsdf_status gsdf_energy_visibility(gsdf_energy* e, const float* psi_dev, const float* g_dev, const double* T_dev,
+                                   uint32_t* nu_dev);
+
+/* Evaluate E at (psi, g, rho, T) with visibility nu (all device; rho 3 n FP32; nu in the bit-set
+ * layout of gsdf_energy_visibility, any bits the caller chooses; lambda_geo finite).  E_dev (device, 3 FP64) receives (E, E_p, E_g); E_g = 0 if lambda_geo = 0.
+ * Gradients (device; NULL = not wanted; dpsi, dg, drho all or none):
+ *   dpsi (n), dg (3 n), drho (3 n) FP32: dE/dpsi, dE/dg, dE/drho;
+ *   dT   (n_frames x 16 FP64): dE/dT_ab for the 12 entries of each T = [R t] as free variables
+ *        (row-major 4 x 4, last row 0) -- the gradient an autograd caller chains through;
+ *   dxi  (n_frames x 6 FP64): dE/dxi for the left perturbation T_i <- exp(xi^) T_i at xi = 0,
+ *        xi = (omega, upsilon).
+ * grad_scale_dev: NULL or one device FP64 that multiplies every gradient (not E): the incoming
+ * gradient of an autograd backward.  Asynchronous; no device allocation. */
+gsdf_status gsdf_energy_eval(gsdf_energy* e, const float* psi_dev, const float* g_dev, const float* rho_dev,
+                             const double* T_dev, const uint32_t* nu_dev, double lambda_geo,
+                             const double* grad_scale_dev, double* E_dev, float* dpsi_dev, float* dg_dev,
+                             float* drho_dev, double* dT_dev, double* dxi_dev);
+
 /* Static description of a status code. */
 const char* gsdf_status_string(gsdf_status s);
 

@@ -87,6 +87,14 @@ _SIGS = {
     "gsdf_track_step_dense_noalloc": (C.c_int, [C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p,
                                                 _P(C.c_int32), _P(C.c_int32), C.c_float, C.c_float, C.c_double,
                                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gsdf_energy_create": (C.c_int, [C.c_int64, C.c_void_p, C.c_float, C.c_int32, _P(gsdf_intrinsics), C.c_void_p,
+                                     C.c_void_p, C.c_void_p, _P(C.c_void_p)]),
+    "gsdf_energy_destroy": (C.c_int, [C.c_void_p]),
+    "gsdf_energy_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gsdf_energy_visibility": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gsdf_energy_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -196,6 +204,37 @@ def gsdf_track_step_dense_noalloc(depth_ptr: int, K: gsdf_intrinsics, A_ptr: int
 
 def gsdf_status_string(s: int) -> str:
     return load_library().gsdf_status_string(s).decode()
+
+
+def gsdf_energy_create(n_voxels: int, m_ptr: int, voxel_size: float, n_frames: int, K: gsdf_intrinsics,
+                       rgb_ptr: int, depth_ptr: int, stream: int = 0) -> int:
+    e = C.c_void_p()
+    _check(load_library().gsdf_energy_create(n_voxels, C.c_void_p(m_ptr or None), voxel_size, n_frames, C.byref(K),
+                                             C.c_void_p(rgb_ptr), C.c_void_p(depth_ptr), C.c_void_p(stream or None),
+                                             C.byref(e)), "gsdf_energy_create")
+    return e.value
+
+
+def gsdf_energy_destroy(e: int) -> int:
+    return load_library().gsdf_energy_destroy(C.c_void_p(e))
+
+
+def gsdf_energy_set_stream(e: int, stream: int) -> int:
+    return load_library().gsdf_energy_set_stream(C.c_void_p(e), C.c_void_p(stream or None))
+
+
+def gsdf_energy_visibility(e: int, psi_ptr: int, g_ptr: int, T_ptr: int, nu_ptr: int) -> int:
+    return load_library().gsdf_energy_visibility(C.c_void_p(e), C.c_void_p(psi_ptr or None), C.c_void_p(g_ptr or None),
+                                                 C.c_void_p(T_ptr), C.c_void_p(nu_ptr or None))
+
+
+def gsdf_energy_eval(e: int, psi_ptr: int, g_ptr: int, rho_ptr: int, T_ptr: int, nu_ptr: int, lambda_geo: float,
+                     grad_scale_ptr: int, E_ptr: int, dpsi_ptr: int = 0, dg_ptr: int = 0, drho_ptr: int = 0,
+                     dT_ptr: int = 0, dxi_ptr: int = 0) -> int:
+    v = lambda x: C.c_void_p(x or None)  # noqa: E731
+    return load_library().gsdf_energy_eval(C.c_void_p(e), v(psi_ptr), v(g_ptr), v(rho_ptr), v(T_ptr), v(nu_ptr),
+                                           lambda_geo, v(grad_scale_ptr), v(E_ptr), v(dpsi_ptr), v(dg_ptr),
+                                           v(drho_ptr), v(dT_ptr), v(dxi_ptr))
 
 
 # -------------------------------------------------------------------------------------------
@@ -359,3 +398,109 @@ class Batch:
         t, c = C.c_int32(), C.c_int32()
         _check(load_library().gsdf_batch_autotune(C.c_void_p(self.b), C.byref(t), C.byref(c)), "gsdf_batch_autotune")
         return t.value, c.value
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if t is not None and t.numel() > 0 else 0
+
+
+class Energy:
+    """The photometric + geometric voxel energy over a fixed voxel list and keyframe set (see
+    include/gsdf.h, gsdf_energy_*).  Tensors are CUDA tensors: m (n, 3) int32, rgb (F, H, W, 3)
+    float32, depth (F, H, W) float32; later calls take psi (n,) and g, rho (n, 3) float32 and
+    poses (F, 4, 4) float64 (camera -> world)."""
+
+    def __init__(self, m, voxel_size: float, K: gsdf_intrinsics, rgb, depth, stream=None):
+        import torch
+
+        self.torch = torch
+        self.n = int(m.shape[0])
+        self.F = int(rgb.shape[0])
+        for name, t, dt in (("m", m, torch.int32), ("rgb", rgb, torch.float32), ("depth", depth, torch.float32)):
+            if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor")
+        if tuple(rgb.shape) != (self.F, K.height, K.width, 3) or tuple(depth.shape) != (self.F, K.height, K.width):
+            raise ValueError("rgb / depth shapes do not match the intrinsics")
+        self.K = K
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.e = gsdf_energy_create(self.n, _ptr(m), voxel_size, self.F, K, rgb.data_ptr(), depth.data_ptr(),
+                                    st.cuda_stream)
+
+    def close(self):
+        if getattr(self, "e", None):
+            gsdf_energy_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        _check(gsdf_energy_set_stream(self.e, self.torch.cuda.current_stream().cuda_stream), "gsdf_energy_set_stream")
+
+    def visibility(self, psi, g, poses):
+        """nu (n, ceil(F / 32)) int32 on the device: bit i mod 32 of word i // 32 of voxel j is nu_ij."""
+        self._stream()
+        nu = self.torch.empty((self.n, (self.F + 31) // 32), dtype=self.torch.int32, device=poses.device)
+        _check(gsdf_energy_visibility(self.e, _ptr(psi), _ptr(g), poses.data_ptr(), _ptr(nu)), "gsdf_energy_visibility")
+        return nu
+
+    def eval(self, psi, g, rho, poses, nu, lambda_geo: float, grad: bool = True, grad_scale=None):
+        """E (3,) float64 = (E, E_p, E_g); with grad also dpsi, dg, drho (float32), dT (F, 4, 4) and
+        dxi (F, 6) (float64)."""
+        torch = self.torch
+        self._stream()
+        dev = poses.device
+        E = torch.empty(3, dtype=torch.float64, device=dev)
+        if not grad:
+            _check(gsdf_energy_eval(self.e, _ptr(psi), _ptr(g), _ptr(rho), poses.data_ptr(), _ptr(nu), lambda_geo,
+                                    _ptr(grad_scale), E.data_ptr()), "gsdf_energy_eval")
+            return E
+        dpsi = torch.empty((self.n,), dtype=torch.float32, device=dev)
+        dg = torch.empty((self.n, 3), dtype=torch.float32, device=dev)
+        drho = torch.empty((self.n, 3), dtype=torch.float32, device=dev)
+        dT = torch.empty((self.F, 4, 4), dtype=torch.float64, device=dev)
+        dxi = torch.empty((self.F, 6), dtype=torch.float64, device=dev)
+        _check(gsdf_energy_eval(self.e, _ptr(psi), _ptr(g), _ptr(rho), poses.data_ptr(), _ptr(nu), lambda_geo,
+                                _ptr(grad_scale), E.data_ptr(), _ptr(dpsi), _ptr(dg), _ptr(drho), dT.data_ptr(),
+                                dxi.data_ptr()), "gsdf_energy_eval")
+        return E, dpsi, dg, drho, dT, dxi
+
+
+def _voxel_energy_function():
+    import torch
+
+    class VoxelEnergy(torch.autograd.Function):
+        """E(psi, g, rho, poses) as a differentiable scalar.  The forward pass evaluates the energy
+        only; the backward pass re-runs the kernels with gradients (every per-pixel lookup is
+        recomputed, nothing per pixel is kept), scaled on the device by the incoming gradient."""
+
+        @staticmethod
+        def forward(ctx, psi, g, rho, poses, energy, nu, lambda_geo):
+            ctx.energy, ctx.nu, ctx.lambda_geo = energy, nu, float(lambda_geo)
+            ctx.save_for_backward(psi, g, rho, poses)
+            return energy.eval(psi, g, rho, poses, nu, ctx.lambda_geo, grad=False)[0]
+
+        @staticmethod
+        def backward(ctx, gE):
+            psi, g, rho, poses = ctx.saved_tensors
+            gE = gE.to(torch.float64).contiguous()
+            _, dpsi, dg, drho, dT, _ = ctx.energy.eval(psi, g, rho, poses, ctx.nu, ctx.lambda_geo, grad=True,
+                                                       grad_scale=gE)
+            return dpsi, dg, drho, dT, None, None, None
+
+    return VoxelEnergy
+
+
+_VoxelEnergy = None
+
+
+def voxel_energy(psi, g, rho, poses, energy: Energy, nu, lambda_geo: float):
+    """Differentiable E = E_p + lambda E_g (torch.autograd.Function around gsdf_energy_eval).
+    The gradient of poses is dE/dT for the entries of each 4 x 4 matrix (last row 0)."""
+    global _VoxelEnergy
+    if _VoxelEnergy is None:
+        _VoxelEnergy = _voxel_energy_function()
+    return _VoxelEnergy.apply(psi, g, rho, poses, energy, nu, lambda_geo)
