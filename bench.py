@@ -73,12 +73,18 @@ def measured_hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+# the sources each profiled kernel is compiled from
+KERNEL_SOURCES = {
+    "track_kernel": ("track.cu", "track_device.cuh", "gsdf_internal.cuh"),
+    "integrate_kernel": ("integrate.cu", "integrate_device.cuh", "gsdf_internal.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2111_13652_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -92,7 +98,7 @@ def profiled_traffic(kernel):
         if "=" in line and not line.startswith("#"):
             k, v = line.strip().split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_sha") != kernel_source_hash():
+    if kv.get("kernel_source_sha") != kernel_source_hash(kernel):
         return None
     try:
         return float(kv["dram_bytes_per_launch"])
