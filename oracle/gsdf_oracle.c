@@ -859,3 +859,77 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
     E[2] = Eg;
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* oriented point cloud and its 2x2x2 upsampling (Sec. 4.3)                                    */
+/* ------------------------------------------------------------------------------------------ */
+
+size_t orc_points(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int level,
+                  orc_point* out, size_t cap) {
+    const float half = 0.5f * voxel_size, quarter = 0.25f * voxel_size;
+    const double vs64 = (double)voxel_size;
+    size_t count = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        /* FP32 index path: ghat and psi ghat of the voxel */
+        const float gj[3] = {(float)g[3 * j], (float)g[3 * j + 1], (float)g[3 * j + 2]};
+        const float ps = (float)psi[j];
+        float n2 = gj[0] * gj[0];
+        n2 = n2 + gj[1] * gj[1];
+        n2 = n2 + gj[2] * gj[2];
+        if (!(n2 > 0.0f)) continue;
+        const float nr = sqrtf(n2);
+        float gh[3];
+        for (int k = 0; k < 3; ++k) gh[k] = gj[k] / nr;
+        /* FP64 values */
+        const double* g64 = g + 3 * j;
+        const double gn = sqrt(g64[0] * g64[0] + g64[1] * g64[1] + g64[2] * g64[2]);
+        const double gh64[3] = {g64[0] / gn, g64[1] / gn, g64[2] / gn};
+        if (level == 0) {
+            int keep = 1;
+            for (int k = 0; k < 3; ++k) {
+                const float sk = ps * gh[k];
+                keep &= fabsf(sk) <= half;
+            }
+            if (!keep) continue;
+            if (count < cap) {
+                orc_point* o = out + count;
+                o->sub = -1;
+                for (int k = 0; k < 3; ++k) {
+                    o->m[k] = m[3 * j + k];
+                    o->p[k] = vs64 * (double)m[3 * j + k] - psi[j] * gh64[k];
+                    o->n[k] = -gh64[k];
+                }
+            }
+            ++count;
+            continue;
+        }
+        for (int sub = 0; sub < 8; ++sub) {
+            float d[3];
+            for (int k = 0; k < 3; ++k) d[k] = ((sub >> k) & 1) ? quarter : -quarter;
+            /* Taylor distance of the subvoxel centre, Eq. (taylor): psi + ghat . delta */
+            float t = gh[0] * d[0];
+            t = t + gh[1] * d[1];
+            t = t + gh[2] * d[2];
+            const float pc = ps + t;
+            int keep = 1;
+            for (int k = 0; k < 3; ++k) {
+                const float sk = pc * gh[k];
+                keep &= fabsf(sk) <= quarter;
+            }
+            if (!keep) continue;
+            if (count < cap) {
+                orc_point* o = out + count;
+                o->sub = sub;
+                double pc64 = psi[j];
+                for (int k = 0; k < 3; ++k) pc64 += gh64[k] * (double)d[k];
+                for (int k = 0; k < 3; ++k) {
+                    o->m[k] = m[3 * j + k];
+                    o->p[k] = vs64 * (double)m[3 * j + k] + (double)d[k] - pc64 * gh64[k];
+                    o->n[k] = -gh64[k];
+                }
+            }
+            ++count;
+        }
+    }
+    return count;
+}

@@ -134,6 +134,27 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
                const float* const* depth, const uint8_t* nu, double lambda_geo, double E[3], double* dpsi,
                double* dg, double* drho, double* dxi, double* dT);
 
+/* ---------------------------------------------------------------------------------------------
+ * Oriented point cloud (Sec. 4.3, "Oriented point cloud extraction") from a voxel list.
+ *   level 0: voxel j gives the point v_j - psi_j ghat_j with normal -ghat_j when
+ *            |psi_j ghat_j| <= v_s / 2 on every axis;
+ *   level 1: each voxel is split into 2 x 2 x 2 subvoxels with centres c = v + delta,
+ *            delta_k = +-v_s / 4; a subvoxel's distance is the Taylor value of Eq. (taylor),
+ *            psi_c = psi + ghat . delta, and it gives the point c - psi_c ghat (normal -ghat) when
+ *            |psi_c ghat| <= v_s / 4 on every axis.
+ * Decisions on the FP32 index path (psi, g rounded to FP32; order of operations in the source),
+ * values in FP64.  Points follow the list order, subvoxels in order sx + 2 sy + 4 sz.  Voxels with
+ * g = 0 give nothing.  Returns the number of points (writes at most cap). */
+typedef struct {
+    int32_t m[3];
+    int32_t sub; /* -1 at level 0, else the subvoxel index sx + 2 sy + 4 sz */
+    double p[3];
+    double n[3];
+} orc_point;
+
+size_t orc_points(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int level,
+                  orc_point* out, size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

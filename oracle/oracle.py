@@ -89,6 +89,9 @@ def lib():
                                  C.c_int, P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(P(C.c_float)),
                                  P(C.c_uint8), C.c_double, P(C.c_double), P(C.c_double), P(C.c_double),
                                  P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.orc_points.restype = C.c_size_t
+        L.orc_points.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), C.c_float, C.c_int,
+                                 C.c_void_p, C.c_size_t]
         _lib = L
     return _lib
 
@@ -292,3 +295,21 @@ def energy(m, psi, g, rho, voxel_size, cam, poses, rgbs, depths, nu, lambda_geo,
     if grad:
         return E, dpsi, dg, drho, dxi, dT
     return E
+
+
+POINT_DTYPE = np.dtype([("m", np.int32, 3), ("sub", np.int32), ("p", np.float64, 3), ("n", np.float64, 3)],
+                       align=True)
+
+
+def points(m, psi, g, voxel_size, level):
+    """Oriented points of a voxel list (Sec. 4.3): level 0 the voxels' own points, level 1 the 2x2x2
+    Taylor upsampling.  Structured array with fields m, sub, p, n."""
+    m = np.ascontiguousarray(m, np.int32)
+    psi = np.ascontiguousarray(psi, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    n = len(psi)
+    cap = n * (8 if level else 1)
+    out = np.zeros(max(cap, 1), POINT_DTYPE)
+    k = lib().orc_points(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), _ptr(g, C.c_double), voxel_size, int(level),
+                         out.ctypes.data, cap)
+    return out[:k]
