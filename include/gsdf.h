@@ -139,6 +139,16 @@ typedef struct {
     float w;
 } gsdf_voxel;
 
+/* One oriented surface point, as returned by gsdf_extract_points (40 bytes): the point p, its unit
+ * normal n (= -ghat, pointing out of the surface), the voxel m it comes from and, after 2x2x2
+ * upsampling, the subvoxel sub = sx + 2 sy + 4 sz (-1 without upsampling). */
+typedef struct {
+    int32_t m[3];
+    int32_t sub;
+    float p[3];
+    float n[3];
+} gsdf_point;
+
 typedef struct gsdf_handle gsdf_handle;
 
 /* Create a map on the current CUDA device.  Allocates the table, the voxel payload (zeroed:
@@ -207,6 +217,20 @@ gsdf_status gsdf_extract_voxels(gsdf_handle* h, gsdf_voxel* host_out, size_t cap
  * Round trip extract -> load -> extract reproduces m, g and w exactly and psi to within one
  * FP32 rounding.  Synchronous; may allocate temporary device memory. */
 gsdf_status gsdf_load_voxels(gsdf_handle* h, const gsdf_voxel* host_in, size_t n);
+
+/* Oriented point cloud of the map (Sec. 4.3).  level 0: every voxel with W > 0 and g != 0 whose
+ * surface point lies in its own cube, |psi ghat| <= v_s / 2 on every axis, gives the point
+ * v - psi ghat with normal -ghat.  level 1 (geometry upsampling): every such voxel is split into
+ * 2 x 2 x 2 subvoxels with centres c = v + delta, delta_k = +-v_s / 4; a subvoxel's distance is the
+ * Taylor value of Eq. (taylor), psi_c = psi + ghat . delta, and it gives c - psi_c ghat when
+ * |psi_c ghat| <= v_s / 4 on every axis.  Decisions are taken in FP32 with correctly rounded
+ * operations in a fixed order (ghat_k = g_k / sqrt((g0 g0 + g1 g1) + g2 g2), psi_c = psi +
+ * ((ghat0 d0 + ghat1 d1) + ghat2 d2), psi = (W psi) / W as stored), so they are reproducible.
+ * Order: the voxel order of gsdf_extract_voxels, subvoxels by increasing sub.  *count_out receives
+ * the number of points even if it exceeds capacity (then only the first `capacity` are written and
+ * GSDF_ERR_CAPACITY is returned).  Synchronous; may allocate temporary device memory. */
+gsdf_status gsdf_extract_points(gsdf_handle* h, int32_t level, gsdf_point* host_out, size_t capacity,
+                                size_t* count_out);
 
 /* Number of allocated hash blocks (dense: number of 512-voxel chunks).  Synchronous. */
 gsdf_status gsdf_num_blocks(gsdf_handle* h, int64_t* n_out);

@@ -1,4 +1,5 @@
-// Extraction of every voxel with W > 0 in a canonical order, and checkpoint loading.
+// Extraction of every voxel with W > 0 in a canonical order, the oriented point cloud of Sec. 4.3
+// (and its 2x2x2 Taylor upsampling) in the same order, and checkpoint loading.
 //
 // Hashed maps: the occupied slots' block keys are collected, sorted (bitonic sort in global
 // memory; keys are unique, so the order is total), counted, prefix-summed, and each block's
@@ -225,6 +226,35 @@ struct DevBuf {
         if (e_ != cudaSuccess) return e_;     \
     } while (0)
 
+// The occupied slots' block keys, sorted ascending into keys (a power-of-two buffer padded with
+// the empty key); *n_keys receives their number.  Synchronises the stream.
+static cudaError_t sorted_block_keys(const HashMap& hm, long long n_slots, cudaStream_t st, unsigned grid,
+                                     DevBuf<unsigned long long>& keys, long long* n_keys_out) {
+    DevBuf<unsigned int> cnt;
+    DevBuf<unsigned long long> tmp;
+    GSDF_CK(cnt.alloc(1));
+    GSDF_CK(tmp.alloc((size_t)n_slots));
+    GSDF_CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned int), st));
+    collect_keys_kernel<<<grid, 256, 0, st>>>(hm.keys, n_slots, tmp.p, cnt.p);
+    GSDF_CK(cudaGetLastError());
+    unsigned int n_keys = 0;
+    GSDF_CK(cudaMemcpyAsync(&n_keys, cnt.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    GSDF_CK(cudaStreamSynchronize(st));
+    const long long N = next_pow2(n_keys > 0 ? n_keys : 1);
+    GSDF_CK(keys.alloc((size_t)N));
+    GSDF_CK(cudaMemsetAsync(keys.p, 0xFF, sizeof(unsigned long long) * (size_t)N, st));
+    if (n_keys)
+        GSDF_CK(cudaMemcpyAsync(keys.p, tmp.p, sizeof(unsigned long long) * n_keys, cudaMemcpyDeviceToDevice, st));
+    for (long long k = 2; k <= N; k <<= 1)
+        for (long long j = k >> 1; j > 0; j >>= 1) {
+            bitonic_step_kernel<<<grid, 256, 0, st>>>(keys.p, N, j, k);
+            GSDF_CK(cudaGetLastError());
+        }
+    GSDF_CK(cudaStreamSynchronize(st));
+    *n_keys_out = n_keys;
+    return cudaSuccess;
+}
+
 cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
                            cudaStream_t st, int num_sms, gsdf_voxel** out_dev, long long* n_out) {
     *out_dev = nullptr;
@@ -233,28 +263,7 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap1
     DevBuf<unsigned long long> keys;
     long long n_chunks = 0, dense_voxels = 0;
     if (hm) {
-        DevBuf<unsigned int> cnt;
-        DevBuf<unsigned long long> tmp;
-        GSDF_CK(cnt.alloc(1));
-        GSDF_CK(tmp.alloc((size_t)n_slots));
-        GSDF_CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned int), st));
-        collect_keys_kernel<<<grid, 256, 0, st>>>(hm->keys, n_slots, tmp.p, cnt.p);
-        GSDF_CK(cudaGetLastError());
-        unsigned int n_keys = 0;
-        GSDF_CK(cudaMemcpyAsync(&n_keys, cnt.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-        GSDF_CK(cudaStreamSynchronize(st));
-        const long long N = next_pow2(n_keys > 0 ? n_keys : 1);
-        GSDF_CK(keys.alloc((size_t)N));
-        GSDF_CK(cudaMemsetAsync(keys.p, 0xFF, sizeof(unsigned long long) * (size_t)N, st));
-        if (n_keys)
-            GSDF_CK(cudaMemcpyAsync(keys.p, tmp.p, sizeof(unsigned long long) * n_keys, cudaMemcpyDeviceToDevice, st));
-        for (long long k = 2; k <= N; k <<= 1)
-            for (long long j = k >> 1; j > 0; j >>= 1) {
-                bitonic_step_kernel<<<grid, 256, 0, st>>>(keys.p, N, j, k);
-                GSDF_CK(cudaGetLastError());
-            }
-        GSDF_CK(cudaStreamSynchronize(st));
-        n_chunks = n_keys;
+        GSDF_CK(sorted_block_keys(*hm, n_slots, st, grid, keys, &n_chunks));
     } else {
         dense_voxels = (long long)dm->dims[0] * dm->dims[1] * dm->dims[2];
         n_chunks = (dense_voxels + kBlockVoxels - 1) / kBlockVoxels;
@@ -285,6 +294,236 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap1
     chunk_write_kernel<<<cgrid, kBlockVoxels, 0, st>>>(sorted, n_chunks, base.p, offsets.p, A, W, dense_voxels,
                                                        dx, dy, ox, oy, oz, h16 ? h16->H : nullptr,
                                                        h16 ? h16->scale : nullptr, out.p);
+    GSDF_CK(cudaGetLastError());
+    GSDF_CK(cudaStreamSynchronize(st));
+    *out_dev = out.release();
+    *n_out = total;
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------------
+// oriented point cloud (Sec. 4.3)
+// ------------------------------------------------------------------------------------------
+
+struct PointSrc {  // where a chunk's voxels live and how to decode them
+    const unsigned long long* sorted;  // hashed: sorted block keys (chunk c = block c); dense: null
+    const long long* base;             // first payload index of each chunk (-1: none)
+    const float4* A;
+    const float* W;
+    const ushort4* H16;
+    const float* scale16;
+    long long dense_voxels;
+    int dx, dy, ox, oy, oz;
+    float vs;
+    int level;
+};
+
+// Voxel coordinate of thread t (local index) in chunk c.
+__device__ __forceinline__ void chunk_voxel_m(const PointSrc& s, long long c, long long i, int t, int m[3]) {
+    if (s.sorted) {
+        int b[3];
+        unpack_block(s.sorted[c], b);
+        m[0] = b[0] * 8 + (t & 7);
+        m[1] = b[1] * 8 + ((t >> 3) & 7);
+        m[2] = b[2] * 8 + (t >> 6);
+    } else {
+        m[0] = s.ox + (int)(i % s.dx);
+        m[1] = s.oy + (int)((i / s.dx) % s.dy);
+        m[2] = s.oz + (int)(i / ((long long)s.dx * s.dy));
+    }
+}
+
+// The points of one voxel on the FP32 index path: bit q of the result keeps point q (level 0: q = 0;
+// level 1: subvoxel q = sx + 2 sy + 4 sz).  gh receives ghat, psi the voxel's distance.
+__device__ __forceinline__ unsigned voxel_point_mask(const PointSrc& s, long long i, float gh[3], float& psi) {
+    const float w = s.W[i];
+    if (!(w > 0.0f)) return 0u;
+    float g[3];
+    if (s.H16) {  // FP16 payload: psi = sigma_b psi~, g = W gbar
+        const ushort4 h = s.H16[i];
+        psi = __half2float(__ushort_as_half(h.x)) * s.scale16[i >> 9];
+        g[0] = __half2float(__ushort_as_half(h.y)) * w;
+        g[1] = __half2float(__ushort_as_half(h.z)) * w;
+        g[2] = __half2float(__ushort_as_half(h.w)) * w;
+    } else {
+        const float4 a = s.A[i];
+        psi = __fdiv_rn(a.x, w);
+        g[0] = a.y;
+        g[1] = a.z;
+        g[2] = a.w;
+    }
+    float n2 = __fmul_rn(g[0], g[0]);
+    n2 = __fadd_rn(n2, __fmul_rn(g[1], g[1]));
+    n2 = __fadd_rn(n2, __fmul_rn(g[2], g[2]));
+    if (!(n2 > 0.0f)) return 0u;
+    const float nr = __fsqrt_rn(n2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gh[k] = __fdiv_rn(g[k], nr);
+    if (s.level == 0) {
+        const float half = 0.5f * s.vs;
+        bool keep = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) keep &= fabsf(__fmul_rn(psi, gh[k])) <= half;
+        return keep ? 1u : 0u;
+    }
+    const float quarter = 0.25f * s.vs;
+    unsigned mask = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float d0 = (q & 1) ? quarter : -quarter, d1 = (q & 2) ? quarter : -quarter;
+        const float d2 = (q & 4) ? quarter : -quarter;
+        // Taylor distance of the subvoxel centre, Eq. (taylor): psi + ghat . delta
+        const float t = __fadd_rn(__fadd_rn(__fmul_rn(gh[0], d0), __fmul_rn(gh[1], d1)), __fmul_rn(gh[2], d2));
+        const float pc = __fadd_rn(psi, t);
+        const bool keep = fabsf(__fmul_rn(pc, gh[0])) <= quarter && fabsf(__fmul_rn(pc, gh[1])) <= quarter &&
+                          fabsf(__fmul_rn(pc, gh[2])) <= quarter;
+        mask |= keep ? (1u << q) : 0u;
+    }
+    return mask;
+}
+
+__device__ __forceinline__ long long chunk_index(const PointSrc& s, long long c, int t, bool& in) {
+    const long long b0 = s.base[c];
+    const long long i = b0 + t;
+    in = b0 >= 0 && ((s.sorted != nullptr) || (i < s.dense_voxels));
+    return i;
+}
+
+__global__ void points_count_kernel(PointSrc s, long long n_chunks, unsigned int* counts) {
+    __shared__ unsigned int cnt;
+    for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        bool in;
+        const long long i = chunk_index(s, c, threadIdx.x, in);
+        float gh[3], psi;
+        const unsigned k = in ? __popc(voxel_point_mask(s, i, gh, psi)) : 0u;
+        unsigned w = k;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&cnt, w);
+        __syncthreads();
+        if (threadIdx.x == 0) counts[c] = cnt;
+        __syncthreads();
+    }
+}
+
+__global__ void points_write_kernel(PointSrc s, long long n_chunks, const long long* __restrict__ offsets,
+                                    gsdf_point* out) {
+    __shared__ unsigned int warp_off[kBlockVoxels / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        bool in;
+        const long long i = chunk_index(s, c, threadIdx.x, in);
+        float gh[3], psi = 0.0f;
+        const unsigned mask = in ? voxel_point_mask(s, i, gh, psi) : 0u;
+        const unsigned k = __popc(mask);
+        unsigned incl = k;  // inclusive scan of the points per thread within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_off[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned run = 0;
+            for (int w = 0; w < kBlockVoxels / 32; ++w) {
+                const unsigned x = warp_off[w];
+                warp_off[w] = run;
+                run += x;
+            }
+        }
+        __syncthreads();
+        if (mask) {
+            long long pos = offsets[c] + warp_off[warp] + incl - k;
+            int m[3];
+            chunk_voxel_m(s, c, i, threadIdx.x, m);
+            const float vm[3] = {__fmul_rn(s.vs, (float)m[0]), __fmul_rn(s.vs, (float)m[1]), __fmul_rn(s.vs, (float)m[2])};
+            const float quarter = 0.25f * s.vs;
+            for (int q = 0; q < 8; ++q) {
+                if (!((mask >> q) & 1u)) continue;
+                gsdf_point o;
+                o.m[0] = m[0];
+                o.m[1] = m[1];
+                o.m[2] = m[2];
+                o.sub = s.level == 0 ? -1 : q;
+                float pc = psi;
+                float cpos[3] = {vm[0], vm[1], vm[2]};
+                if (s.level != 0) {
+                    const float d[3] = {(q & 1) ? quarter : -quarter, (q & 2) ? quarter : -quarter,
+                                        (q & 4) ? quarter : -quarter};
+                    const float t =
+                        __fadd_rn(__fadd_rn(__fmul_rn(gh[0], d[0]), __fmul_rn(gh[1], d[1])), __fmul_rn(gh[2], d[2]));
+                    pc = __fadd_rn(psi, t);
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) cpos[kk] = __fadd_rn(vm[kk], d[kk]);
+                }
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    o.p[kk] = __fsub_rn(cpos[kk], __fmul_rn(pc, gh[kk]));
+                    o.n[kk] = -gh[kk];
+                }
+                out[pos++] = o;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t extract_points(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
+                           float voxel_size, int level, cudaStream_t st, int num_sms, gsdf_point** out_dev,
+                           long long* n_out) {
+    *out_dev = nullptr;
+    *n_out = 0;
+    const unsigned grid = (unsigned)(num_sms * 8);
+    DevBuf<unsigned long long> keys;
+    long long n_chunks = 0, dense_voxels = 0;
+    if (hm) {
+        GSDF_CK(sorted_block_keys(*hm, n_slots, st, grid, keys, &n_chunks));
+    } else {
+        dense_voxels = (long long)dm->dims[0] * dm->dims[1] * dm->dims[2];
+        n_chunks = (dense_voxels + kBlockVoxels - 1) / kBlockVoxels;
+    }
+    if (n_chunks == 0) return cudaSuccess;
+    DevBuf<long long> base, offsets;
+    DevBuf<unsigned int> counts;
+    GSDF_CK(base.alloc((size_t)n_chunks));
+    GSDF_CK(counts.alloc((size_t)n_chunks));
+    GSDF_CK(offsets.alloc((size_t)n_chunks + 1));
+    const HashMap hmv = hm ? *hm : HashMap{};
+    const float* W = h16 ? h16->W : (hm ? hm->W : dm->W);
+    const unsigned long long* sorted = hm ? keys.p : nullptr;
+    const unsigned cgrid = (unsigned)(n_chunks < (long long)num_sms * 16 ? n_chunks : (long long)num_sms * 16);
+    // chunk bases (the voxel counts of chunk_count_kernel are not needed here)
+    chunk_count_kernel<<<cgrid, kBlockVoxels, 0, st>>>(hmv, sorted, n_chunks, dense_voxels, W, base.p, counts.p);
+    GSDF_CK(cudaGetLastError());
+    PointSrc src{};
+    src.sorted = sorted;
+    src.base = base.p;
+    src.A = hm ? hm->A : dm->A;
+    src.W = W;
+    src.H16 = h16 ? h16->H : nullptr;
+    src.scale16 = h16 ? h16->scale : nullptr;
+    src.dense_voxels = dense_voxels;
+    src.dx = dm ? dm->dims[0] : 0;
+    src.dy = dm ? dm->dims[1] : 0;
+    src.ox = dm ? dm->origin[0] : 0;
+    src.oy = dm ? dm->origin[1] : 0;
+    src.oz = dm ? dm->origin[2] : 0;
+    src.vs = voxel_size;
+    src.level = level;
+    points_count_kernel<<<cgrid, kBlockVoxels, 0, st>>>(src, n_chunks, counts.p);
+    GSDF_CK(cudaGetLastError());
+    scan_kernel<<<1, 1024, 0, st>>>(counts.p, n_chunks, offsets.p);
+    GSDF_CK(cudaGetLastError());
+    long long total = 0;
+    GSDF_CK(cudaMemcpyAsync(&total, offsets.p + n_chunks, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    GSDF_CK(cudaStreamSynchronize(st));
+    if (total == 0) return cudaSuccess;
+    DevBuf<gsdf_point> out;
+    GSDF_CK(out.alloc((size_t)total));
+    points_write_kernel<<<cgrid, kBlockVoxels, 0, st>>>(src, n_chunks, offsets.p, out.p);
     GSDF_CK(cudaGetLastError());
     GSDF_CK(cudaStreamSynchronize(st));
     *out_dev = out.release();

@@ -320,6 +320,9 @@ namespace gsdf {
 // extraction / checkpoint (extract.cu).  *out_dev is allocated with cudaMalloc; caller frees.
 cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
                            cudaStream_t st, int num_sms, gsdf_voxel** out_dev, long long* n_out);
+cudaError_t extract_points(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
+                           float voxel_size, int level, cudaStream_t st, int num_sms, gsdf_point** out_dev,
+                           long long* n_out);
 cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, float trunc,
                         const gsdf_voxel* in_dev, long long n, int* err, unsigned int* n_blocks, cudaStream_t st,
                         int num_sms);

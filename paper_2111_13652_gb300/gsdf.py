@@ -58,6 +58,13 @@ class gsdf_voxel(C.Structure):
 
 
 VOXEL_DTYPE = np.dtype([("m", "<i4", 3), ("psi", "<f4"), ("g", "<f4", 3), ("w", "<f4")])
+
+
+class gsdf_point(C.Structure):
+    _fields_ = [("m", C.c_int32 * 3), ("sub", C.c_int32), ("p", C.c_float * 3), ("n", C.c_float * 3)]
+
+
+POINT_DTYPE = np.dtype([("m", "<i4", 3), ("sub", "<i4"), ("p", "<f4", 3), ("n", "<f4", 3)])
 TRACK_STATS_BYTES = C.sizeof(gsdf_track_stats)
 INTEGRATE_STATS_BYTES = C.sizeof(gsdf_integrate_stats)
 
@@ -74,6 +81,7 @@ _SIGS = {
     "gsdf_extract_voxels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
     "gsdf_load_voxels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "gsdf_num_blocks": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
+    "gsdf_extract_points": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
     "gsdf_sync": (C.c_int, [C.c_void_p]),
     "gsdf_status_string": (C.c_char_p, [C.c_int]),
     "gsdf_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, _P(C.c_void_p)]),
@@ -173,6 +181,13 @@ def gsdf_extract_voxels(h: int, out: np.ndarray | None, capacity: int):
     n = C.c_size_t()
     ptr = out.ctypes.data if out is not None else None
     st = load_library().gsdf_extract_voxels(C.c_void_p(h), C.c_void_p(ptr), capacity, C.byref(n))
+    return st, n.value
+
+
+def gsdf_extract_points(h: int, level: int, out: np.ndarray | None, capacity: int):
+    n = C.c_size_t()
+    ptr = out.ctypes.data if out is not None else None
+    st = load_library().gsdf_extract_points(C.c_void_p(h), level, C.c_void_p(ptr), capacity, C.byref(n))
     return st, n.value
 
 
@@ -344,6 +359,20 @@ class Map:
             _check(st, "gsdf_extract_voxels")
             assert n2 == n
         return out
+
+    def extract_points(self, level: int = 0, capacity: int | None = None) -> np.ndarray:
+        """Oriented surface points (m, sub, p, n) of the map, level 0 or 1 (2x2x2 upsampling).  With a
+        capacity large enough the library runs once; otherwise it is asked for the count first."""
+        if capacity is None:
+            st, capacity = gsdf_extract_points(self.h, level, None, 0)
+            if st not in (GSDF_OK, GSDF_ERR_CAPACITY):
+                _check(st, "gsdf_extract_points")
+        out = np.zeros(capacity, POINT_DTYPE)
+        st, n = gsdf_extract_points(self.h, level, out, capacity)
+        if st == GSDF_ERR_CAPACITY:
+            return self.extract_points(level, n)
+        _check(st, "gsdf_extract_points")
+        return out[:n]
 
     def load(self, vox: np.ndarray):
         _check(gsdf_load_voxels(self.h, vox), "gsdf_load_voxels")
