@@ -418,6 +418,41 @@ int orc_taylor(const orc_map* map, const double P[3], const int32_t m[3], double
     return 0;
 }
 
+int orc_trilinear(const orc_map* map, const double P[3], const int32_t b[3], double* d, double grad[3]) {
+    const double vs = (double)map->prm.voxel_size;
+    double a[3], c[8];
+    for (int k = 0; k < 3; ++k) a[k] = (P[k] - vs * (double)b[k]) / vs;
+    for (int q = 0; q < 8; ++q) {
+        const int32_t m[3] = {b[0] + (q & 1), b[1] + ((q >> 1) & 1), b[2] + ((q >> 2) & 1)};
+        const orc_entry* e = orc_find(map, m);
+        if (!e || !(e->w > 0.0)) return 1;
+        c[q] = e->psi;
+    }
+    double s = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        const int ix = q & 1, iy = (q >> 1) & 1, iz = (q >> 2) & 1;
+        const double wx = ix ? a[0] : 1.0 - a[0], wy = iy ? a[1] : 1.0 - a[1], wz = iz ? a[2] : 1.0 - a[2];
+        const double sx = ix ? 1.0 : -1.0, sy = iy ? 1.0 : -1.0, sz = iz ? 1.0 : -1.0;
+        s += c[q] * wx * wy * wz;
+        gx += c[q] * sx * wy * wz;
+        gy += c[q] * wx * sy * wz;
+        gz += c[q] * wx * wy * sz;
+    }
+    *d = s;
+    grad[0] = gx / vs;
+    grad[1] = gy / vs;
+    grad[2] = gz / vs;
+    return 0;
+}
+
+/* lowest corner of the interpolation cell of P on the FP32 index path: floor(P (1/v_s)) */
+static void orc_cell(const float P[3], float inv_vs, int32_t b[3]) {
+    for (int i = 0; i < 3; ++i) {
+        const float s = P[i] * inv_vs;
+        b[i] = (int32_t)floorf(s);
+    }
+}
+
 int orc_track_reduce(const orc_map* map, const float* depth, const orc_intrinsics* K,
                      const double T_wc[16], orc_track_stats* st) {
     const orc_params* prm = &map->prm;
@@ -437,10 +472,17 @@ int orc_track_reduce(const orc_map* map, const float* depth, const orc_intrinsic
             int32_t m[3];
             orc_ray_world(K, &rc, q.R, u, v, dw);
             orc_ray_point(dw, q.t, D, Pf);
-            orc_round_voxel(Pf, rc.inv_vs, m);
             double P[3] = {Pf[0], Pf[1], Pf[2]}, gh[3], r;
-            if (orc_taylor(map, P, m, &r, gh) != 0) continue;
-            /* J = d r / d xi for T <- exp(xi^) T, xi = (omega, upsilon): (P x ghat, ghat) */
+            if (prm->tracker == 1) {
+                /* direct SDF baseline: trilinear d and its gradient (not normalised) */
+                orc_cell(Pf, rc.inv_vs, m);
+                if (orc_trilinear(map, P, m, &r, gh) != 0) continue;
+            } else {
+                orc_round_voxel(Pf, rc.inv_vs, m);
+                if (orc_taylor(map, P, m, &r, gh) != 0) continue;
+            }
+            /* J = d r / d xi for T <- exp(xi^) T, xi = (omega, upsilon): (P x ghat, ghat), ghat
+             * standing for the gradient of the residual's model (grad d for the trilinear one) */
             double J[6] = {P[1] * gh[2] - P[2] * gh[1], P[2] * gh[0] - P[0] * gh[2],
                            P[0] * gh[1] - P[1] * gh[0], gh[0], gh[1], gh[2]};
             double ar = fabs(r);

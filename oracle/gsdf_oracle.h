@@ -43,6 +43,8 @@ typedef struct {
     float huber_delta;
     float cos_max_angle;
     double damping; /* relative Levenberg-Marquardt damping, 0 = plain Gauss-Newton */
+    int tracker;    /* 0: Eq. (taylor), one voxel; 1: trilinear interpolation of psi over the 8 voxels
+                       of the cell, Eqs. (dir_dist), (dir_grad) (the direct SDF tracker baseline) */
 } orc_params;
 
 typedef struct {
@@ -90,6 +92,11 @@ int orc_solve6(const double H21[21], const double b[6], double damping, int64_t 
 void orc_se3_exp(const double xi[6], double T[16]);
 /* Taylor model at world point P using voxel m: returns 0 if usable, fills r and ghat */
 int orc_taylor(const orc_map* map, const double P[3], const int32_t m[3], double* r, double ghat[3]);
+/* Eqs. (dir_dist), (dir_grad) with trilinear interpolation over the cell whose lowest corner is
+ * voxel b: with a = P / v_s - b, d(P) = sum_c psi_c prod_k (a_k or 1 - a_k) over the 8 corners, and
+ * grad d its exact gradient (differences of psi along each axis, bilinearly weighted, / v_s).
+ * Returns 0 if all 8 corners exist with W > 0. */
+int orc_trilinear(const orc_map* map, const double P[3], const int32_t b[3], double* d, double grad[3]);
 /* FP32 index path: world point of pixel (u, v) at depth D and its rounded voxel coordinate */
 void orc_pixel_point(const orc_intrinsics* K, const double T_wc[16], int u, int v, float D,
                      float P_out[3], int32_t m_out[3], float voxel_size);

@@ -37,7 +37,8 @@ class Intrinsics(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("voxel_size", C.c_float), ("truncation", C.c_float), ("weight_eps", C.c_float),
-                ("huber_delta", C.c_float), ("cos_max_angle", C.c_float), ("damping", C.c_double)]
+                ("huber_delta", C.c_float), ("cos_max_angle", C.c_float), ("damping", C.c_double),
+                ("tracker", C.c_int)]
 
 
 class VoxelOut(C.Structure):
@@ -77,6 +78,7 @@ def lib():
         L.orc_solve6.argtypes = [P(C.c_double), P(C.c_double), C.c_double, C.c_int64, P(C.c_double)]
         L.orc_se3_exp.argtypes = [P(C.c_double), P(C.c_double)]
         L.orc_taylor.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32), P(C.c_double), P(C.c_double)]
+        L.orc_trilinear.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int32), P(C.c_double), P(C.c_double)]
         L.orc_pixel_point.argtypes = [P(Intrinsics), P(C.c_double), C.c_int, C.c_int, C.c_float,
                                       P(C.c_float), P(C.c_int32), C.c_float]
         L.orc_normal.argtypes = [P(C.c_float), P(Intrinsics), P(Params), C.c_int, C.c_int, P(C.c_float)]
@@ -105,11 +107,12 @@ def intrinsics(cam) -> Intrinsics:
 
 
 def params(voxel_size, truncation=None, weight_eps=None, huber_delta=None,
-           cos_max_angle=0.25881904, damping=0.0) -> Params:
+           cos_max_angle=0.25881904, damping=0.0, tracker=0) -> Params:
+    """tracker 0: Eq. (taylor); 1: trilinear interpolation over the 8 voxels of the cell."""
     vs = float(voxel_size)
     return Params(vs, 5 * vs if truncation is None else truncation,
                   vs if weight_eps is None else weight_eps,
-                  vs if huber_delta is None else huber_delta, cos_max_angle, damping)
+                  vs if huber_delta is None else huber_delta, cos_max_angle, damping, tracker)
 
 
 def _pose(T) -> np.ndarray:
@@ -190,6 +193,17 @@ class OracleMap:
         if lib().orc_taylor(self.h, _ptr(Pa, C.c_double), _ptr(ma, C.c_int32), C.byref(r), _ptr(gh, C.c_double)):
             return None
         return r.value, gh
+
+    def trilinear(self, P, b):
+        """Eqs. (dir_dist), (dir_grad): trilinear d and grad d at P over the cell with lowest corner
+        voxel b; None unless all 8 corners are observed."""
+        Pa = np.ascontiguousarray(P, np.float64)
+        ba = np.ascontiguousarray(b, np.int32)
+        d = C.c_double()
+        gr = np.zeros(3)
+        if lib().orc_trilinear(self.h, _ptr(Pa, C.c_double), _ptr(ba, C.c_int32), C.byref(d), _ptr(gr, C.c_double)):
+            return None
+        return d.value, gr
 
 
 def stats_H(st: TrackStats) -> np.ndarray:
