@@ -57,6 +57,7 @@ typedef enum {
 
 enum { GSDF_GRID_DENSE = 0, GSDF_GRID_HASHED = 1 };
 enum { GSDF_PAYLOAD_F32 = 0, GSDF_PAYLOAD_F16 = 1 };
+enum { GSDF_TRACKER_TAYLOR = 0, GSDF_TRACKER_TRILINEAR = 1 };
 
 /* Pinhole intrinsics (Sec. 5.3 uses 640x480 TUM frames, depth cut off at 3.5 m). */
 typedef struct {
@@ -90,7 +91,15 @@ typedef struct {
  *   max_touched_blocks  FP16 payload only: entries of the per-frame accumulator table (a power
  *                  of two, at most hash_slots; keep it at least twice the blocks one frame
  *                  touches).  A frame whose blocks do not find an entry within 64 probes is fused
- *                  partially and reports GSDF_ERR_CAPACITY */
+ *                  partially and reports GSDF_ERR_CAPACITY
+ *   tracker        the model of gsdf_track_step.  GSDF_TRACKER_TAYLOR (the method, Eq. taylor):
+ *                  one voxel lookup per pixel.  GSDF_TRACKER_TRILINEAR (the direct SDF tracker
+ *                  the paper compares against, Eqs. dir_dist and dir_grad, Sec. 6): psi is
+ *                  interpolated trilinearly over the 8 voxels of the cell containing P (lowest
+ *                  corner floor(P (1/v_s)), FP32), r = d(P), J = (P x grad d, grad d) with the
+ *                  interpolant's gradient; a pixel whose cell has an unobserved corner is
+ *                  skipped.  FP32 payload only; not accepted by gsdf_batch_create.
+ */
 typedef struct {
     int32_t grid_kind;
     int32_t dense_dims[3];
@@ -105,7 +114,7 @@ typedef struct {
     int32_t max_probe;
     int32_t payload;             /* GSDF_PAYLOAD_F32 or GSDF_PAYLOAD_F16 (hashed maps only) */
     int32_t max_touched_blocks;  /* FP16 payload: blocks a single frame may update (>= 1) */
-    int32_t pad;
+    int32_t tracker;             /* GSDF_TRACKER_TAYLOR or GSDF_TRACKER_TRILINEAR */
 } gsdf_config;
 
 /* Written by gsdf_track_step into device memory.  H is the upper triangle (row-major, 21

@@ -293,7 +293,7 @@ gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda
     if (!out || !handles || n < 1 || n > 65536) return GSDF_ERR_INVALID_ARG;
     *out = nullptr;
     for (int s = 0; s < n; ++s)
-        if (!handles[s] || handles[s]->fp16) return GSDF_ERR_INVALID_ARG;
+        if (!handles[s] || handles[s]->fp16 || handles[s]->cfg.tracker != GSDF_TRACKER_TAYLOR) return GSDF_ERR_INVALID_ARG;
     gsdf_batch* b = new (std::nothrow) gsdf_batch();
     if (!b) return GSDF_ERR_OOM;
     b->n = n;

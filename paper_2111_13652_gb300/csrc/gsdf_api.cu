@@ -47,6 +47,8 @@ gsdf_status check_config(const gsdf_config* c) {
         const long long a = c->max_touched_blocks;
         if (a < 1 || a > c->hash_slots || (a & (a - 1)) != 0) return GSDF_ERR_INVALID_ARG;
     }
+    if (c->tracker != GSDF_TRACKER_TAYLOR && c->tracker != GSDF_TRACKER_TRILINEAR) return GSDF_ERR_INVALID_ARG;
+    if (c->tracker == GSDF_TRACKER_TRILINEAR && c->payload != GSDF_PAYLOAD_F32) return GSDF_ERR_INVALID_ARG;
     return GSDF_OK;
 }
 
@@ -70,6 +72,9 @@ gsdf_status check_intr(const gsdf_intrinsics* K, Intr* out) {
 cudaError_t track_once(const gsdf_handle* h, const float* depth, const Intr& ki, double* T_wc, gsdf_track_stats* stats,
                        cudaStream_t st) {
     if (h->fp16) return launch_track16(h->hm16, depth, ki, h->prm, T_wc, stats, h->sc, h->num_sms, st);
+    if (h->cfg.tracker == GSDF_TRACKER_TRILINEAR)
+        return launch_track_trilinear(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, depth, ki, h->prm,
+                                      T_wc, stats, h->sc, h->num_sms, st);
     return launch_track(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, depth, ki, h->prm, T_wc, stats,
                         h->sc, h->num_sms, st);
 }

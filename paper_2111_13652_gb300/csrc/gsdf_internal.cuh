@@ -303,6 +303,10 @@ cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* dep
                          const Params& prm, double* T_wc, gsdf_track_stats* stats,
                          const Scratch& sc, int num_sms, cudaStream_t st);
 
+cudaError_t launch_track_trilinear(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
+                                   const Params& prm, double* T_wc, gsdf_track_stats* stats, const Scratch& sc,
+                                   int num_sms, cudaStream_t st);
+
 cudaError_t launch_track16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm, double* T_wc,
                            gsdf_track_stats* stats, const Scratch& sc, int num_sms, cudaStream_t st);
 

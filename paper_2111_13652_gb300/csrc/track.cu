@@ -1,5 +1,7 @@
 // Tracking: one Gauss-Newton step of Eq. (tracking) with the first-order model Eq. (taylor)
-// (Sec. 4.1), reduced and solved on the device (Sec. 5.1: Gauss-Newton + Cholesky).
+// (Sec. 4.1), reduced and solved on the device (Sec. 5.1: Gauss-Newton + Cholesky).  The same
+// kernel, instantiated with kTrilinear, is the trilinear 8-lookup baseline of Eqs. (dir_dist),
+// (dir_grad).
 //
 // One kernel per step.  Each thread walks pixels with a grid stride, evaluates the one-lookup
 // Taylor residual and its Jacobian and accumulates the 30 unique terms (21 of H, 6 of b, E,
@@ -12,7 +14,7 @@
 
 namespace gsdf {
 
-template <class Map>
+template <class Map, bool kTrilinear = false>
 __global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
 track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, double* T_wc,
              gsdf_track_stats* stats, Scratch sc) {
@@ -23,8 +25,12 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
     const int n_px = K.width * K.height;
-    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x)
-        track_pixel(map, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x) {
+        if (kTrilinear)
+            track_pixel_trilinear(map, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+        else
+            track_pixel(map, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+    }
     block_reduce_terms(sh, acc);
     // block b adds into accumulator copy b mod kAccumCopies (spreads same-address atomics)
     if (!add_partial_and_ticket(sh, sc.accum, sc.counter, blockIdx.x, gridDim.x)) return;
@@ -56,6 +62,22 @@ cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* dep
         track_kernel<DenseMap><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*dm, depth, K, prm, T_wc, stats, sc);
     else
         track_kernel<HashMap><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*hm, depth, K, prm, T_wc, stats, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_track_trilinear(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
+                                   const Params& prm, double* T_wc, gsdf_track_stats* stats, const Scratch& sc,
+                                   int num_sms, cudaStream_t st) {
+    const long long n_px = (long long)K.width * K.height;
+    long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
+    long long cap = (long long)kTrackBlocksPerSM * num_sms;
+    if (cap > sc.max_track_blocks) cap = sc.max_track_blocks;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (dm)
+        track_kernel<DenseMap, true><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*dm, depth, K, prm, T_wc, stats, sc);
+    else
+        track_kernel<HashMap, true><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*hm, depth, K, prm, T_wc, stats, sc);
     return cudaGetLastError();
 }
 

@@ -315,6 +315,70 @@ __device__ __forceinline__ void track_pixel(const Map& map, const float* __restr
     acc[29] += ar > delta ? 1.0f : 0.0f;
 }
 
+// The direct SDF tracker the paper compares against (Eqs. dir_dist, dir_grad): psi interpolated
+// trilinearly over the 8 voxels of the cell containing P -- 8 lookups per pixel -- with r = d(P)
+// and J = (P x grad d, grad d), grad d the interpolant's exact gradient.  The cell's lowest corner
+// is floor(P (1/v_s)) on the FP32 index path; a = (P - v_s b) / v_s with v_s b split exactly.
+// Same Huber weighting and terms as track_pixel.
+template <class Map>
+__device__ __forceinline__ void track_pixel_trilinear(const Map& map, const float* __restrict__ depth,
+                                                      const Intr& K, const float* R, const float* t,
+                                                      const Params& prm, int pix, float (&acc)[32]) {
+    const float D = __ldg(depth + pix);
+    if (!depth_ok(D, K.depth_max)) return;
+    const int v = pix / K.width;
+    const int u = pix - v * K.width;
+    float dw[3], P[3];
+    ray_world(K, R, u, v, dw);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P[i] = ray_coord(D, dw[i], t[i]);
+    int b[3];
+    float a[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        b[i] = (int)floorf(__fmul_rn(P[i], prm.inv_vs));
+        const float bf = (float)b[i];
+        const float vh = __fmul_rn(prm.vs, bf);
+        const float vl = __fmaf_rn(prm.vs, bf, -vh);
+        a[i] = __fsub_rn(__fsub_rn(P[i], vh), vl) * prm.inv_vs;
+    }
+    float d = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // each corner is accumulated as soon as it is read
+        const long long idx = map.find(b[0] + (q & 1), b[1] + ((q >> 1) & 1), b[2] + ((q >> 2) & 1));
+        if (idx < 0) return;
+        float c, g0, g1, g2;
+        if (!map.voxel(idx, c, g0, g1, g2)) return;
+        const float wx = (q & 1) ? a[0] : 1.0f - a[0];
+        const float wy = (q & 2) ? a[1] : 1.0f - a[1];
+        const float wz = (q & 4) ? a[2] : 1.0f - a[2];
+        d += c * wx * wy * wz;
+        gx += ((q & 1) ? c : -c) * wy * wz;
+        gy += ((q & 2) ? c : -c) * wx * wz;
+        gz += ((q & 4) ? c : -c) * wx * wy;
+    }
+    gx *= prm.inv_vs;
+    gy *= prm.inv_vs;
+    gz *= prm.inv_vs;
+    const float r = d;
+    const float J[6] = {P[1] * gz - P[2] * gy, P[2] * gx - P[0] * gz, P[0] * gy - P[1] * gx, gx, gy, gz};
+    const float delta = prm.huber;
+    const float ar = fabsf(r);
+    const float w = ar <= delta ? 1.0f : __fdividef(delta, ar);
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float wJi = w * J[i];
+#pragma unroll
+        for (int j = i; j < 6; ++j) acc[q++] += wJi * J[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[21 + i] += w * J[i] * r;
+    acc[27] += w * r * r;
+    acc[28] += 1.0f;
+    acc[29] += ar > delta ? 1.0f : 0.0f;
+}
+
 // Block reduction of the per-thread terms: warps reduce-scatter (lane l <- term l), then a fixed
 // FP64 tree over the warps leaves the block totals in part[0][0..29].  All threads call it.
 __device__ __forceinline__ void block_reduce_terms(TrackShared& sh, float (&acc)[32]) {

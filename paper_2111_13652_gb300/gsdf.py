@@ -27,6 +27,8 @@ GSDF_GRID_DENSE = 0
 GSDF_GRID_HASHED = 1
 GSDF_PAYLOAD_F32 = 0
 GSDF_PAYLOAD_F16 = 1
+GSDF_TRACKER_TAYLOR = 0
+GSDF_TRACKER_TRILINEAR = 1
 
 
 class gsdf_intrinsics(C.Structure):
@@ -39,7 +41,7 @@ class gsdf_config(C.Structure):
                 ("voxel_size", C.c_float), ("truncation", C.c_float), ("weight_eps", C.c_float),
                 ("huber_delta", C.c_float), ("cos_max_angle", C.c_float), ("damping", C.c_double),
                 ("hash_slots", C.c_int64), ("max_probe", C.c_int32), ("payload", C.c_int32),
-                ("max_touched_blocks", C.c_int32), ("pad", C.c_int32)]
+                ("max_touched_blocks", C.c_int32), ("tracker", C.c_int32)]
 
 
 class gsdf_track_stats(C.Structure):
@@ -263,7 +265,7 @@ def intrinsics(cam) -> gsdf_intrinsics:
 
 def make_config(voxel_size, *, dense_dims=None, dense_origin=(0, 0, 0), truncation=None, weight_eps=None,
                 huber_delta=None, cos_max_angle=0.25881904, damping=0.0, hash_slots=1 << 16,
-                max_probe=128, fp16=False, max_touched_blocks=None) -> gsdf_config:
+                max_probe=128, fp16=False, max_touched_blocks=None, tracker=0) -> gsdf_config:
     vs = float(voxel_size)
     c = gsdf_config()
     c.grid_kind = GSDF_GRID_HASHED if dense_dims is None else GSDF_GRID_DENSE
@@ -280,6 +282,7 @@ def make_config(voxel_size, *, dense_dims=None, dense_origin=(0, 0, 0), truncati
     c.max_probe = max_probe
     c.payload = GSDF_PAYLOAD_F16 if fp16 else GSDF_PAYLOAD_F32
     c.max_touched_blocks = max(1, hash_slots // 4) if max_touched_blocks is None else max_touched_blocks  # power of 2
+    c.tracker = tracker
     return c
 
 
