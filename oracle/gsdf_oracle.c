@@ -903,6 +903,187 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* photometric bundle adjustment step (Sec. 4.2)                                                */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Colour and its image gradient at the projection of voxel j in keyframe i, if the pair counts:
+ * FP32 index path for the decisions (orc_project32, in-image test, cell), FP64 values.  Returns 0
+ * if the pair does not count.  p, gh: the surface point and ghat; x: camera coordinates. */
+static int orc_pair_colour(const int32_t* m, const double* psi, const double* g, int64_t j, float voxel_size,
+                           const double* T, const orc_pose32* q32, const orc_intrinsics* K, const float* img,
+                           double I[3], double dIdu[3], double dIdv[3], double p[3], double gh[3], double x[3]) {
+    const int Wd = K->width, Hd = K->height;
+    orc_proj32 o;
+    if (!orc_project32(m, psi, g, j, voxel_size, q32, K, &o)) return 0;
+    if (!(o.u >= 0.0f && o.u <= (float)(Wd - 1) && o.v >= 0.0f && o.v <= (float)(Hd - 1))) return 0;
+    int x0 = (int)floorf(o.u), y0 = (int)floorf(o.v);
+    if (x0 > Wd - 2) x0 = Wd - 2;
+    if (y0 > Hd - 2) y0 = Hd - 2;
+    double gn;
+    if (!orc_surface_point(m, psi, g, j, (double)voxel_size, p, gh, &gn)) return 0;
+    orc_to_camera(T, p, x);
+    const double u = K->fx * x[0] / x[2] + K->cx, v = K->fy * x[1] / x[2] + K->cy;
+    const double a = u - x0, b = v - y0;
+    for (int c = 0; c < 3; ++c) {
+        const double I00 = img[((size_t)y0 * Wd + x0) * 3 + c], I01 = img[((size_t)y0 * Wd + x0 + 1) * 3 + c];
+        const double I10 = img[((size_t)(y0 + 1) * Wd + x0) * 3 + c];
+        const double I11 = img[((size_t)(y0 + 1) * Wd + x0 + 1) * 3 + c];
+        I[c] = (1 - a) * (1 - b) * I00 + a * (1 - b) * I01 + (1 - a) * b * I10 + a * b * I11;
+        dIdu[c] = (1 - b) * (I01 - I00) + b * (I11 - I10);
+        dIdv[c] = (1 - a) * (I10 - I00) + a * (I11 - I01);
+    }
+    return 1;
+}
+
+static void orc_add_normal(double A[6][6], double bb[6], const double J[6], double r, double w) {
+    for (int i = 0; i < 6; ++i) {
+        for (int k = i; k < 6; ++k) A[i][k] += w * J[i] * J[k];
+        bb[i] += w * J[i] * r;
+    }
+}
+
+int orc_ba_step(int64_t n, const int32_t* m, double* psi, const double* g, double* rho, float voxel_size, int n_frames,
+                const orc_intrinsics* K, double* poses, const float* const* rgb, const float* const* depth,
+                const uint8_t* nu, double lambda_geo, double damping, int flags, orc_track_stats* st, double* psi_H,
+                double* psi_b) {
+    const double vs = (double)voxel_size;
+    double* sum = (double*)calloc((size_t)(n > 0 ? n : 1) * 4, sizeof(double));
+    double* hp = (double*)calloc((size_t)(n > 0 ? n : 1) * 2, sizeof(double));
+    orc_key_index* keys = (orc_key_index*)malloc(sizeof(orc_key_index) * (size_t)(n > 0 ? n : 1));
+    if (!sum || !hp || !keys) {
+        free(sum);
+        free(hp);
+        free(keys);
+        return -1;
+    }
+    /* 1. mean colour, Eq. (mean_color), over the pairs that count */
+    for (int i = 0; i < n_frames; ++i) {
+        orc_pose32 q32;
+        orc_round_pose(poses + 16 * i, &q32);
+        for (int64_t j = 0; j < n; ++j) {
+            if (!nu[(size_t)i * n + j]) continue;
+            double I[3], du[3], dv[3], p[3], gh[3], x[3];
+            if (!orc_pair_colour(m, psi, g, j, voxel_size, poses + 16 * i, &q32, K, rgb[i], I, du, dv, p, gh, x))
+                continue;
+            for (int c = 0; c < 3; ++c) sum[4 * j + c] += I[c];
+            sum[4 * j + 3] += 1.0;
+        }
+    }
+    for (int64_t j = 0; j < n; ++j)
+        for (int c = 0; c < 3; ++c) rho[3 * j + c] = sum[4 * j + 3] > 0.0 ? sum[4 * j + c] / sum[4 * j + 3] : 0.0;
+    /* 2. Gauss-Newton terms with rho fixed (the decoupled energies of Eq. rgb_cost_pose) */
+    for (int64_t j = 0; j < n; ++j) {
+        keys[j].m[0] = m[3 * j];
+        keys[j].m[1] = m[3 * j + 1];
+        keys[j].m[2] = m[3 * j + 2];
+        keys[j].idx = j;
+    }
+    qsort(keys, (size_t)n, sizeof(orc_key_index), orc_cmp_key);
+    const orc_recip rc = orc_recips(K, voxel_size);
+    for (int i = 0; i < n_frames; ++i) {
+        const double* T = poses + 16 * i;
+        orc_pose32 q32;
+        orc_round_pose(T, &q32);
+        double A[6][6] = {{0}}, bb[6] = {0}, E = 0.0;
+        int64_t nres = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (!nu[(size_t)i * n + j]) continue;
+            double I[3], du[3], dv[3], p[3], gh[3], x[3];
+            if (!orc_pair_colour(m, psi, g, j, voxel_size, T, &q32, K, rgb[i], I, du, dv, p, gh, x)) continue;
+            const double z = x[2];
+            for (int c = 0; c < 3; ++c) {
+                const double r = I[c] - rho[3 * j + c];
+                /* dI/dx through the pinhole, then q = R dI/dx = dI/dp */
+                const double dx[3] = {du[c] * K->fx / z, dv[c] * K->fy / z,
+                                      -(du[c] * K->fx * x[0] + dv[c] * K->fy * x[1]) / (z * z)};
+                double qv[3];
+                for (int r_ = 0; r_ < 3; ++r_)
+                    qv[r_] = T[4 * r_ + 0] * dx[0] + T[4 * r_ + 1] * dx[1] + T[4 * r_ + 2] * dx[2];
+                /* left perturbation: dp_cam/domega via x = R^T (p - t): dI/domega = q x p, dI/dupsilon = -q */
+                const double J[6] = {qv[1] * p[2] - qv[2] * p[1], qv[2] * p[0] - qv[0] * p[2],
+                                     qv[0] * p[1] - qv[1] * p[0], -qv[0], -qv[1], -qv[2]};
+                orc_add_normal(A, bb, J, r, 1.0);
+                E += r * r;
+                ++nres;
+                const double jp = -(qv[0] * gh[0] + qv[1] * gh[1] + qv[2] * gh[2]); /* dp/dpsi = -ghat */
+                hp[2 * j] += jp * jp;
+                hp[2 * j + 1] += jp * r;
+            }
+        }
+        for (int v = 0; v < K->height && lambda_geo != 0.0; ++v) {
+            for (int u = 0; u < K->width; ++u) {
+                const float D = depth[i][(size_t)v * K->width + u];
+                if (!orc_depth_ok(D, K->depth_max)) continue;
+                float dw[3], Pf[3];
+                orc_key_index key;
+                orc_ray_world(K, &rc, q32.R, u, v, dw);
+                orc_ray_point(dw, q32.t, D, Pf);
+                orc_round_voxel(Pf, rc.inv_vs, key.m);
+                const orc_key_index* hit =
+                    (const orc_key_index*)bsearch(&key, keys, (size_t)n, sizeof(orc_key_index), orc_cmp_key);
+                if (!hit) continue;
+                const int64_t j = hit->idx;
+                const double* gj = g + 3 * j;
+                const double gn = sqrt(gj[0] * gj[0] + gj[1] * gj[1] + gj[2] * gj[2]);
+                if (!(gn > 0.0)) continue;
+                const double P[3] = {Pf[0], Pf[1], Pf[2]};
+                double gh[3], r = psi[j];
+                for (int k = 0; k < 3; ++k) {
+                    gh[k] = gj[k] / gn;
+                    r += gh[k] * (P[k] - vs * (double)key.m[k]);
+                }
+                const double J[6] = {P[1] * gh[2] - P[2] * gh[1], P[2] * gh[0] - P[0] * gh[2],
+                                     P[0] * gh[1] - P[1] * gh[0], gh[0], gh[1], gh[2]};
+                orc_add_normal(A, bb, J, r, lambda_geo);
+                E += lambda_geo * r * r;
+                ++nres;
+                hp[2 * j] += lambda_geo; /* dr/dpsi = 1 */
+                hp[2 * j + 1] += lambda_geo * r;
+            }
+        }
+        orc_track_stats* s = st + i;
+        int idx = 0;
+        for (int a = 0; a < 6; ++a)
+            for (int k = a; k < 6; ++k) s->H[idx++] = A[a][k];
+        for (int a = 0; a < 6; ++a) {
+            s->b[a] = bb[a];
+            s->xi[a] = 0.0;
+        }
+        s->energy = E;
+        s->n_valid = nres;
+        s->n_huber = 0;
+        s->status = 0;
+    }
+    /* 3. updates */
+    for (int i = 0; i < n_frames && (flags & ORC_BA_POSES); ++i) {
+        orc_track_stats* s = st + i;
+        double xi[6];
+        s->status = orc_solve6(s->H, s->b, damping, s->n_valid, xi);
+        for (int a = 0; a < 6; ++a) s->xi[a] = xi[a];
+        if (s->status) continue;
+        double dT[16], Tn[16];
+        double* T = poses + 16 * i;
+        orc_se3_exp(xi, dT);
+        for (int a = 0; a < 4; ++a)
+            for (int k = 0; k < 4; ++k) {
+                double acc = 0.0;
+                for (int l = 0; l < 4; ++l) acc += dT[4 * a + l] * T[4 * l + k];
+                Tn[4 * a + k] = acc;
+            }
+        memcpy(T, Tn, sizeof(Tn));
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        if (psi_H) psi_H[j] = hp[2 * j];
+        if (psi_b) psi_b[j] = hp[2 * j + 1];
+        if ((flags & ORC_BA_PSI) && hp[2 * j] > 0.0) psi[j] -= hp[2 * j + 1] / ((1.0 + damping) * hp[2 * j]);
+    }
+    free(sum);
+    free(hp);
+    free(keys);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* oriented point cloud and its 2x2x2 upsampling (Sec. 4.3)                                    */
 /* ------------------------------------------------------------------------------------------ */
 

@@ -142,6 +142,29 @@ int orc_energy(int64_t n, const int32_t* m, const double* psi, const double* g, 
                double* dg, double* drho, double* dxi, double* dT);
 
 /* ---------------------------------------------------------------------------------------------
+ * One iteration of photometric bundle adjustment (Sec. 4.2, Eqs. rgb_cost, intensity_proj,
+ * mean_color, rgb_cost_pose), optionally with lambda times the geometric term of Eq. (tracking):
+ *   1. rho_j = mean colour of voxel j over the pairs that count (Eq. mean_color);
+ *   2. with rho held fixed (the decoupled energies E_i of Eq. rgb_cost_pose), per keyframe the
+ *      Gauss-Newton normal equations H_i = sum J J^T, b_i = sum J r of the residuals
+ *      r = I_ij^c - rho_j^c with J = d r / d xi_i for the left perturbation T_i <- exp(xi^) T_i,
+ *      plus lambda times the tracking terms of every keyframe pixel; per voxel the 1-D normal
+ *      equations in psi_j (ghat held fixed, Sec. 4.2): psi_H = sum (dr/dpsi)^2, psi_b = sum
+ *      dr/dpsi r, the geometric residual contributing lambda and lambda r;
+ *   3. if flags & ORC_BA_POSES: xi_i = -(H_i + damping mean(diag H_i) I)^-1 b_i (orc_solve6) and
+ *      T_i <- exp(xi_i^) T_i; if flags & ORC_BA_PSI: psi_j -= psi_b / ((1 + damping) psi_H) for
+ *      psi_H > 0.
+ * Pairs, cells and visibility as in orc_energy.  st[i] receives H, b, E_i (the step's starting
+ * energy of keyframe i: its photometric residuals plus lambda times its geometric ones), the
+ * residual count, the solve status and xi.  rho (3n) is written; psi_H, psi_b (n) may be NULL. */
+#define ORC_BA_POSES 1
+#define ORC_BA_PSI 2
+int orc_ba_step(int64_t n, const int32_t* m, double* psi, const double* g, double* rho, float voxel_size, int n_frames,
+                const orc_intrinsics* K, double* poses, const float* const* rgb, const float* const* depth,
+                const uint8_t* nu, double lambda_geo, double damping, int flags, orc_track_stats* st, double* psi_H,
+                double* psi_b);
+
+/* ---------------------------------------------------------------------------------------------
  * Oriented point cloud (Sec. 4.3, "Oriented point cloud extraction") from a voxel list.
  *   level 0: voxel j gives the point v_j - psi_j ghat_j with normal -ghat_j when
  *            |psi_j ghat_j| <= v_s / 2 on every axis;

@@ -91,6 +91,10 @@ def lib():
                                  C.c_int, P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(P(C.c_float)),
                                  P(C.c_uint8), C.c_double, P(C.c_double), P(C.c_double), P(C.c_double),
                                  P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.orc_ba_step.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double), C.c_float,
+                                  C.c_int, P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(P(C.c_float)),
+                                  P(C.c_uint8), C.c_double, C.c_double, C.c_int, P(TrackStats), P(C.c_double),
+                                  P(C.c_double)]
         L.orc_points.restype = C.c_size_t
         L.orc_points.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), C.c_float, C.c_int,
                                  C.c_void_p, C.c_size_t]
@@ -327,3 +331,31 @@ def points(m, psi, g, voxel_size, level):
     k = lib().orc_points(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), _ptr(g, C.c_double), voxel_size, int(level),
                          out.ctypes.data, cap)
     return out[:k]
+
+
+BA_POSES = 1
+BA_PSI = 2
+
+
+def ba_step(m, psi, g, voxel_size, cam, poses, rgbs, depths, nu, lambda_geo, damping, flags):
+    """One photometric BA iteration (see orc_ba_step).  Returns (psi', rho, poses', stats, psi_H, psi_b):
+    psi' and poses' after the updates selected by flags (BA_POSES | BA_PSI), rho the mean colours the
+    step used, stats a list of per-keyframe TrackStats (H, b, energy, n_valid, status, xi)."""
+    m = np.ascontiguousarray(m, np.int32)
+    psi = np.array(psi, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    nu = np.ascontiguousarray(nu, np.uint8)
+    n, F = len(psi), len(poses)
+    P = np.ascontiguousarray(np.stack([np.asarray(T, np.float64).reshape(16) for T in poses]))
+    keep_r, rptr = _frames_ptrs(rgbs)
+    keep_d, dptr = _frames_ptrs(depths)
+    rho = np.zeros((n, 3))
+    hp, hb = np.zeros(n), np.zeros(n)
+    st = (TrackStats * F)()
+    K = intrinsics(cam)
+    rc = lib().orc_ba_step(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), _ptr(g, C.c_double), _ptr(rho, C.c_double),
+                           voxel_size, F, C.byref(K), _ptr(P, C.c_double), rptr, dptr, _ptr(nu, C.c_uint8),
+                           lambda_geo, damping, int(flags), st, _ptr(hp, C.c_double), _ptr(hb, C.c_double))
+    if rc != 0:
+        raise MemoryError("orc_ba_step failed")
+    return psi, rho, [P[i].reshape(4, 4).copy() for i in range(F)], list(st), hp, hb
