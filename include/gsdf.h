@@ -387,6 +387,30 @@ gsdf_status gsdf_energy_eval(gsdf_energy* e, const float* psi_dev, const float* 
                              const double* grad_scale_dev, double* E_dev, float* dpsi_dev, float* dg_dev,
                              float* drho_dev, double* dT_dev, double* dxi_dev);
 
+/* One iteration of photometric bundle adjustment on the energy's voxels and keyframes (Sec. 4.2,
+ * Eqs. rgb_cost, intensity_proj, mean_color, rgb_cost_pose), optionally with lambda_geo times the
+ * geometric term (every keyframe pixel's Eq. tracking residual):
+ *   1. rho_dev (3 n FP32, written) receives every voxel's mean colour over the pairs that count
+ *      (Eq. mean_color; 0 where none counts);
+ *   2. with rho held fixed -- the decoupled per-keyframe energies of Eq. rgb_cost_pose -- each
+ *      keyframe's Gauss-Newton normal equations H_i = sum J J^T, b_i = sum J r are formed from its
+ *      colour residuals r = I_ij^c - rho_j^c, J = d r / d xi for T_i <- exp(xi^) T_i, plus lambda
+ *      times its pixels' tracking terms; and per voxel the 1-D normal equations in psi_j (ghat
+ *      held fixed, as the paper does; the geometric residual contributes lambda and lambda r);
+ *   3. if flags & GSDF_BA_POSES, every keyframe pose T_dev[i] (FP64, in place) is replaced by
+ *      exp(xi_i^) T_i with (H_i + damping mean(diag H_i) I) xi_i = -b_i (FP64 Cholesky-equivalent
+ *      solve of the tracking step; a degenerate system leaves the pose and sets the status); if
+ *      flags & GSDF_BA_PSI, psi_dev (in place) takes the damped Newton step
+ *      psi_j -= psi_b / ((1 + damping) psi_H) where psi_H > 0.  flags = 0 evaluates only.
+ * Pairs, visibility (nu_dev, the bit set of gsdf_energy_visibility) and decisions as in
+ * gsdf_energy_eval.  stats_dev: NULL or n_frames device gsdf_track_stats, entry i with H_i, b_i,
+ * the keyframe's energy at the start of the step (colour residuals plus lambda times geometric),
+ * the residual count in n_valid, the status and xi_i.  Asynchronous; no device allocation. */
+enum { GSDF_BA_POSES = 1, GSDF_BA_PSI = 2 };
+gsdf_status gsdf_energy_ba_step(gsdf_energy* e, float* psi_dev, const float* g_dev, float* rho_dev, double* T_dev,
+                                const uint32_t* nu_dev, double lambda_geo, double damping, int32_t flags,
+                                gsdf_track_stats* stats_dev);
+
 /* Static description of a status code. */
 const char* gsdf_status_string(gsdf_status s);
 

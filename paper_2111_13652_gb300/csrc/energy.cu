@@ -32,6 +32,7 @@
 #include <new>
 
 #include "gsdf_internal.cuh"
+#include "track_device.cuh"  // FP64 6x6 solve, SE(3) exponential and the 32-term warp reduce-scatter
 
 using namespace gsdf;
 
@@ -80,6 +81,8 @@ struct EnergyArgs {
     double* acc;               // F x kSlots
     float4* vacc;              // n: geometric (dE/dpsi, dE/dg) of each voxel, cleared by merge_kernel
     bool geo_grads;            // vacc holds this evaluation's geometric voxel gradients
+    float4* cacc;              // n: colour sums and pair count of each voxel (bundle adjustment)
+    double* bacc;              // F x 32: Gauss-Newton terms per keyframe (bundle adjustment)
     int* pairs;                // F x n: voxels keyframe i sees, pair_count[i] of them
     unsigned int* pair_count;  // F
     float* dpsi;
@@ -610,6 +613,242 @@ __global__ void __launch_bounds__(kEThreads) merge_kernel(EnergyArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
+// photometric bundle adjustment (one Gauss-Newton iteration; see gsdf_energy_ba_step)
+// ------------------------------------------------------------------------------------------
+
+// Colour (and its image gradient, when dIdu != null) of the projection of voxel j's surface point
+// into keyframe f, if the pair counts (FP32 index path of the decisions, as the energy).
+__device__ __forceinline__ bool pair_colour(const EnergyArgs& a, const EFrame& f, const float4* rgb, long long j,
+                                            SurfPt& sp, float d[3], float x[3], float I[3], float* dIdu,
+                                            float* dIdv) {
+    const int W = a.K.width, H = a.K.height;
+    if (!surface_point32(a.m[3 * j], a.m[3 * j + 1], a.m[3 * j + 2], a.psi[j], a.g[3 * j], a.g[3 * j + 1],
+                         a.g[3 * j + 2], a.vs, sp))
+        return false;
+    float u, v;
+    if (!(project32(sp, f, a.K, d, x, u, v) && u >= 0.0f && u <= (float)(W - 1) && v >= 0.0f && v <= (float)(H - 1)))
+        return false;
+    int x0 = (int)floorf(u), y0 = (int)floorf(v);
+    if (x0 > W - 2) x0 = W - 2;
+    if (y0 > H - 2) y0 = H - 2;
+    const float al = u - (float)x0, be = v - (float)y0;
+    const float4* img = rgb + (long long)y0 * W + x0;
+    const float4 I00 = img[0], I01 = img[1], I10 = img[W], I11 = img[W + 1];
+    const float i00[3] = {I00.x, I00.y, I00.z}, i01[3] = {I01.x, I01.y, I01.z};
+    const float i10[3] = {I10.x, I10.y, I10.z}, i11[3] = {I11.x, I11.y, I11.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        I[c] = (1.0f - al) * (1.0f - be) * i00[c] + al * (1.0f - be) * i01[c] + (1.0f - al) * be * i10[c] +
+               al * be * i11[c];
+        if (dIdu) {
+            dIdu[c] = (1.0f - be) * (i01[c] - i00[c]) + be * (i11[c] - i10[c]);
+            dIdv[c] = (1.0f - al) * (i10[c] - i00[c]) + al * (i11[c] - i01[c]);
+        }
+    }
+    return true;
+}
+
+// Eq. (mean_color), pass 1: colour sums and counts of every voxel over the pairs that count.
+__global__ void __launch_bounds__(kEThreads) colour_sum_kernel(EnergyArgs a) {
+    __shared__ EFrame fr[1];
+    const int i = blockIdx.y;
+    load_frames(fr, a.T + 16 * i, 1);
+    __syncthreads();
+    const float4* rgb = a.rgb + (long long)i * a.K.width * a.K.height;
+    const int* list = a.pairs + (long long)i * a.n;
+    const unsigned cnt = a.pair_count[i];
+    for (unsigned k = blockIdx.x * kEThreads + threadIdx.x; k < cnt; k += gridDim.x * kEThreads) {
+        const long long j = list[k];
+        SurfPt sp;
+        float d[3], x[3], I[3];
+        if (pair_colour(a, fr[0], rgb, j, sp, d, x, I, nullptr, nullptr))
+            atomicAdd(a.cacc + j, make_float4(I[0], I[1], I[2], 1.0f));
+    }
+}
+
+// Pass 2: rho = sums / count (0 for a voxel no pair counts); the sums are cleared by negated reds.
+__global__ void __launch_bounds__(kEThreads) colour_mean_kernel(EnergyArgs a, float* rho) {
+    for (long long j = (long long)blockIdx.x * kEThreads + threadIdx.x; j < a.n; j += (long long)gridDim.x * kEThreads) {
+        const float4 s = a.cacc[j];
+        const float inv = s.w > 0.0f ? 1.0f / s.w : 0.0f;
+        rho[3 * j] = s.x * inv;
+        rho[3 * j + 1] = s.y * inv;
+        rho[3 * j + 2] = s.z * inv;
+        if (s.w != 0.0f) atomicAdd(a.cacc + j, make_float4(-s.x, -s.y, -s.z, -s.w));
+    }
+}
+
+// Adds J J^T (21 terms), J r (6), r^2 and one residual to the per-thread terms, weighted by w.
+__device__ __forceinline__ void add_gn_terms(float (&acc)[32], const float J[6], float r, float w) {
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float wJi = w * J[i];
+#pragma unroll
+        for (int k = i; k < 6; ++k) acc[q++] += wJi * J[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[21 + i] += w * J[i] * r;
+    acc[27] += w * r * r;
+    acc[28] += 1.0f;
+}
+
+// The keyframe's 29 Gauss-Newton terms of this block, added to its FP64 accumulator.
+__device__ __forceinline__ void block_add_gn(float (&acc)[32], double* out) {
+    __shared__ double part[kEWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    part[warp][lane] = (double)warp_reduce_scatter32(acc);
+    __syncthreads();
+    if (threadIdx.x < 29) {
+        double t = 0.0;
+        for (int w = 0; w < kEWarps; ++w) t += part[w][threadIdx.x];
+        if (t != 0.0) atomicAdd(out + threadIdx.x, t);
+    }
+}
+
+// Photometric Gauss-Newton terms with rho fixed (the decoupled energies of Eq. rgb_cost_pose):
+// per pair and channel r = I - rho, J = (q x p, -q) with q = R dI/dx; per voxel (dr/dpsi)^2 and
+// dr/dpsi r with dr/dpsi = -q . ghat, added to vacc.x, vacc.y.
+__global__ void __launch_bounds__(kEThreads) ba_photo_kernel(EnergyArgs a) {
+    __shared__ EFrame fr[1];
+    const int i = blockIdx.y;
+    load_frames(fr, a.T + 16 * i, 1);
+    __syncthreads();
+    const float4* rgb = a.rgb + (long long)i * a.K.width * a.K.height;
+    const int* list = a.pairs + (long long)i * a.n;
+    const unsigned cnt = a.pair_count[i];
+    float acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+    for (unsigned k = blockIdx.x * kEThreads + threadIdx.x; k < cnt; k += gridDim.x * kEThreads) {
+        const long long j = list[k];
+        SurfPt sp;
+        float d[3], x[3], I[3], du[3], dv[3];
+        if (!pair_colour(a, fr[0], rgb, j, sp, d, x, I, du, dv)) continue;
+        const float iz = 1.0f / x[2];
+        const float* R = fr[0].R;
+        float hp = 0.0f, bp = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = I[c] - a.rho[3 * j + c];
+            const float dx[3] = {du[c] * a.K.fx * iz, dv[c] * a.K.fy * iz,
+                                 -(du[c] * a.K.fx * x[0] + dv[c] * a.K.fy * x[1]) * iz * iz};
+            float q[3];
+#pragma unroll
+            for (int r_ = 0; r_ < 3; ++r_) q[r_] = R[3 * r_] * dx[0] + R[3 * r_ + 1] * dx[1] + R[3 * r_ + 2] * dx[2];
+            const float J[6] = {q[1] * sp.p[2] - q[2] * sp.p[1], q[2] * sp.p[0] - q[0] * sp.p[2],
+                                q[0] * sp.p[1] - q[1] * sp.p[0], -q[0], -q[1], -q[2]};
+            add_gn_terms(acc, J, r, 1.0f);
+            const float jp = -(q[0] * sp.gh[0] + q[1] * sp.gh[1] + q[2] * sp.gh[2]);
+            hp += jp * jp;
+            bp += jp * r;
+        }
+        atomicAdd(a.vacc + j, make_float4(hp, bp, 0.0f, 0.0f));
+    }
+    block_add_gn(acc, a.bacc + 32 * i);
+}
+
+// lambda times the tracking terms of every keyframe pixel (Eq. tracking with Eq. taylor); per
+// voxel dr/dpsi = 1.
+__global__ void __launch_bounds__(kEThreads) ba_geo_kernel(EnergyArgs a) {
+    __shared__ EFrame fr[1];
+    const int i = blockIdx.y;
+    load_frames(fr, a.T + 16 * i, 1);
+    __syncthreads();
+    const float lam = (float)a.lambda;
+    const unsigned W = (unsigned)a.K.width;
+    const unsigned npx = W * (unsigned)a.K.height;
+    const float* depth = a.depth + (long long)i * npx;
+    float acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+    for (unsigned px = blockIdx.x * kEThreads + threadIdx.x; px < npx; px += gridDim.x * kEThreads) {
+        const float D = depth[px];
+        if (!depth_ok(D, a.K.depth_max)) continue;
+        const int v = (int)(px / W), u = (int)(px - (unsigned)v * W);
+        float dw[3], P[3];
+        int mv[3];
+        ray_world(a.K, fr[0].R, u, v, dw);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P[k] = ray_coord(D, dw[k], fr[0].t[k]);
+            mv[k] = round_voxel(P[k], a.inv_vs);
+        }
+        const int j = index_find(a.tab, mv[0], mv[1], mv[2]);
+        if (j < 0) continue;
+        const float g0 = a.g[3 * j], g1 = a.g[3 * j + 1], g2 = a.g[3 * j + 2];
+        if (g0 == 0.0f && g1 == 0.0f && g2 == 0.0f) continue;
+        const float n2 = g0 * g0 + g1 * g1 + g2 * g2;
+        const float inr = n2 >= 1e-30f ? rsqrtf(n2) : 1.0f / norm3df(g0, g1, g2);
+        const float gh[3] = {g0 * inr, g1 * inr, g2 * inr};
+        float dd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float mf = (float)mv[k];
+            const float vh = __fmul_rn(a.vs, mf);
+            const float vl = __fmaf_rn(a.vs, mf, -vh);
+            dd[k] = __fsub_rn(__fsub_rn(P[k], vh), vl);
+        }
+        const float r = a.psi[j] + (gh[0] * dd[0] + gh[1] * dd[1] + gh[2] * dd[2]);
+        const float J[6] = {P[1] * gh[2] - P[2] * gh[1], P[2] * gh[0] - P[0] * gh[2], P[0] * gh[1] - P[1] * gh[0],
+                            gh[0], gh[1], gh[2]};
+        add_gn_terms(acc, J, r, lam);
+        atomicAdd(a.vacc + j, make_float4(lam, lam * r, 0.0f, 0.0f));
+    }
+    block_add_gn(acc, a.bacc + 32 * i);
+}
+
+// One warp per keyframe: damped FP64 solve of its 6x6 system, left update exp(xi^) T, statistics;
+// clears the keyframe's accumulator and pair count for the next call.
+__global__ void __launch_bounds__(32) ba_solve_kernel(double* bacc, unsigned int* pair_count, double* T,
+                                                      double damping, int update, gsdf_track_stats* stats) {
+    __shared__ double tot[32], xi[6], dT[16], Ts[16];
+    const int i = blockIdx.x, lane = threadIdx.x;
+    tot[lane] = bacc[32 * i + lane];
+    bacc[32 * i + lane] = 0.0;
+    if (lane < 16) Ts[lane] = T[16 * i + lane];
+    if (lane == 0) pair_count[i] = 0u;
+    __syncwarp();
+    const long long n_valid = (long long)(tot[28] + 0.5);
+    bool ok = false;
+    if (update) {
+        ok = solve6_warp(tot, damping, n_valid, xi);
+        if (ok) se3_exp_warp(xi, dT);
+        if (ok && lane < 12) {
+            const int r = lane >> 2, c = lane & 3;
+            double tn = (dT[4 * r] * Ts[c] + dT[4 * r + 1] * Ts[4 + c]) + dT[4 * r + 2] * Ts[8 + c];
+            if (c == 3) tn += dT[4 * r + 3];
+            T[16 * i + lane] = tn;
+        }
+    }
+    if (stats) {
+        gsdf_track_stats* s = stats + i;
+        if (lane < 21)
+            s->H[lane] = tot[lane];
+        else if (lane < 27)
+            s->b[lane - 21] = tot[lane];
+        if (lane < 6) s->xi[lane] = ok ? xi[lane] : 0.0;
+        if (lane == 0) {
+            s->energy = tot[27];
+            s->n_valid = n_valid;
+            s->n_huber = 0;
+            s->status = (!update || ok) ? (int)GSDF_OK : (int)GSDF_ERR_DEGENERATE;
+            s->pad = 0;
+        }
+    }
+}
+
+// psi_j -= psi_b / ((1 + damping) psi_H) where psi_H > 0 (if update), and vacc cleared.
+__global__ void __launch_bounds__(kEThreads) ba_psi_kernel(EnergyArgs a, float* psi, double damping, int update) {
+    for (long long j = (long long)blockIdx.x * kEThreads + threadIdx.x; j < a.n; j += (long long)gridDim.x * kEThreads) {
+        const float4 v = a.vacc[j];
+        if (v.x == 0.0f && v.y == 0.0f) continue;
+        if (update && v.x > 0.0f) psi[j] -= (float)((double)v.y / ((1.0 + damping) * (double)v.x));
+        atomicAdd(a.vacc + j, make_float4(-v.x, -v.y, 0.0f, 0.0f));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // finish: energies, pose gradients, accumulator reset
 // ------------------------------------------------------------------------------------------
 
@@ -693,6 +932,8 @@ struct gsdf_energy {
     float4* rgb = nullptr;
     float* depth = nullptr;
     float4* vacc = nullptr;  // n
+    float4* cacc = nullptr;  // n: colour sums (bundle adjustment)
+    double* bacc = nullptr;  // kMaxFrames x 32: Gauss-Newton terms (bundle adjustment)
     int* pairs = nullptr;    // F x n
     unsigned int* pair_count = nullptr;
     double* acc = nullptr;
@@ -701,6 +942,7 @@ struct gsdf_energy {
     long long n_blocks = 0;  // 8^3 blocks holding the list's voxels
     int photo_blocks[2] = {0, 0};  // resident grid of photo_kernel<false>, <true>
     int geo_blocks[2] = {0, 0};
+    int ba_photo_blocks = 0, ba_geo_blocks = 0;
 };
 
 namespace {
@@ -710,6 +952,8 @@ void free_energy(gsdf_energy* e) {
     cudaFree(e->tab.slots);
     cudaFree(e->tab.vox);
     cudaFree(e->vacc);
+    cudaFree(e->cacc);
+    cudaFree(e->bacc);
     cudaFree(e->pairs);
     cudaFree(e->pair_count);
     cudaFree(e->rgb);
@@ -733,6 +977,8 @@ EnergyArgs make_args(const gsdf_energy* e) {
     a.tab = e->tab;
     a.acc = e->acc;
     a.vacc = e->vacc;
+    a.cacc = e->cacc;
+    a.bacc = e->bacc;
     a.pairs = e->pairs;
     a.pair_count = e->pair_count;
     return a;
@@ -795,6 +1041,8 @@ gsdf_status gsdf_energy_create(int64_t n_voxels, const int32_t* m_dev, float vox
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
     if (ce == cudaSuccess) ce = cudaMalloc(&e->m, sizeof(int) * 3 * nv);
     if (ce == cudaSuccess) ce = cudaMalloc(&e->vacc, sizeof(float4) * nv);
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->cacc, sizeof(float4) * nv);
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->bacc, sizeof(double) * 32 * kMaxFrames);
     if (ce == cudaSuccess) ce = cudaMalloc(&e->pairs, sizeof(int) * nv * (size_t)n_frames);
     if (ce == cudaSuccess) ce = cudaMalloc(&e->pair_count, sizeof(unsigned int) * kMaxFrames);
     if (ce == cudaSuccess) ce = cudaMalloc(&e->rgb, sizeof(float4) * (size_t)npx);
@@ -808,10 +1056,14 @@ gsdf_status gsdf_energy_create(int64_t n_voxels, const int32_t* m_dev, float vox
     if (ce == cudaSuccess) ce = resident(photo_kernel<true>, e->num_sms, &e->photo_blocks[1]);
     if (ce == cudaSuccess) ce = resident(geo_kernel<false>, e->num_sms, &e->geo_blocks[0]);
     if (ce == cudaSuccess) ce = resident(geo_kernel<true>, e->num_sms, &e->geo_blocks[1]);
+    if (ce == cudaSuccess) ce = resident(ba_photo_kernel, e->num_sms, &e->ba_photo_blocks);
+    if (ce == cudaSuccess) ce = resident(ba_geo_kernel, e->num_sms, &e->ba_geo_blocks);
     cudaStream_t st = e->stream;
     if (n_voxels > 0 && ce == cudaSuccess)
         ce = cudaMemcpyAsync(e->m, m_dev, sizeof(int) * 3 * (size_t)n_voxels, cudaMemcpyDeviceToDevice, st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(e->vacc, 0, sizeof(float4) * nv, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->cacc, 0, sizeof(float4) * nv, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->bacc, 0, sizeof(double) * 32 * kMaxFrames, st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(e->acc, 0, sizeof(double) * kSlots * kMaxFrames, st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(e->pair_count, 0, sizeof(unsigned int) * kMaxFrames, st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(e->err, 0, sizeof(int), st);
@@ -947,6 +1199,41 @@ gsdf_status gsdf_energy_eval(gsdf_energy* e, const float* psi_dev, const float* 
     }
     finish_kernel<<<1, kMaxFrames * kSlots, 0, st>>>(e->acc, e->pair_count, e->F, lambda_geo, T_dev, grad_scale_dev, E_dev,
                                             dT_dev, dxi_dev);
+    return from_cuda(cudaGetLastError());
+}
+
+gsdf_status gsdf_energy_ba_step(gsdf_energy* e, float* psi_dev, const float* g_dev, float* rho_dev, double* T_dev,
+                                const uint32_t* nu_dev, double lambda_geo, double damping, int32_t flags,
+                                gsdf_track_stats* stats_dev) {
+    if (!e || !T_dev || !isfinite(lambda_geo) || !isfinite(damping) || damping < 0.0 || (flags & ~3)) return GSDF_ERR_INVALID_ARG;
+    if (e->n > 0 && (!psi_dev || !g_dev || !rho_dev || !nu_dev)) return GSDF_ERR_INVALID_ARG;
+    EnergyArgs a = make_args(e);
+    a.psi = psi_dev;
+    a.g = g_dev;
+    a.rho = rho_dev;
+    a.T = T_dev;
+    a.nu = (const unsigned*)nu_dev;
+    a.lambda = lambda_geo;
+    cudaStream_t st = e->stream;
+    const long long npx = (long long)e->K.width * e->K.height;
+    const long long need = (e->n + kEThreads - 1) / kEThreads;
+    if (e->n > 0) {
+        const long long chunks = (e->n + kPairChunk - 1) / kPairChunk;
+        pairs_kernel<<<(int)(chunks < e->pairs_blocks ? chunks : e->pairs_blocks), kEThreads, 0, st>>>(a);
+        const dim3 pgrid(columns_for(e->ba_photo_blocks, e->F, need), e->F);
+        colour_sum_kernel<<<pgrid, kEThreads, 0, st>>>(a);
+        colour_mean_kernel<<<grid_for(e->n, e->vis_blocks), kEThreads, 0, st>>>(a, rho_dev);
+        ba_photo_kernel<<<pgrid, kEThreads, 0, st>>>(a);
+    }
+    if (lambda_geo != 0.0) {
+        const long long pneed = (npx + kEThreads - 1) / kEThreads;
+        ba_geo_kernel<<<dim3(columns_for(e->ba_geo_blocks, e->F, pneed), e->F), kEThreads, 0, st>>>(a);
+    }
+    ba_solve_kernel<<<e->F, 32, 0, st>>>(e->bacc, e->pair_count, T_dev, damping, (flags & GSDF_BA_POSES) ? 1 : 0,
+                                         stats_dev);
+    if (e->n > 0)
+        ba_psi_kernel<<<grid_for(e->n, e->vis_blocks), kEThreads, 0, st>>>(a, psi_dev, damping,
+                                                                             (flags & GSDF_BA_PSI) ? 1 : 0);
     return from_cuda(cudaGetLastError());
 }
 

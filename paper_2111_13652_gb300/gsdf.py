@@ -29,6 +29,8 @@ GSDF_PAYLOAD_F32 = 0
 GSDF_PAYLOAD_F16 = 1
 GSDF_TRACKER_TAYLOR = 0
 GSDF_TRACKER_TRILINEAR = 1
+GSDF_BA_POSES = 1
+GSDF_BA_PSI = 2
 
 
 class gsdf_intrinsics(C.Structure):
@@ -102,6 +104,8 @@ _SIGS = {
     "gsdf_energy_destroy": (C.c_int, [C.c_void_p]),
     "gsdf_energy_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gsdf_energy_visibility": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gsdf_energy_ba_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "gsdf_energy_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p]),
@@ -243,6 +247,13 @@ def gsdf_energy_set_stream(e: int, stream: int) -> int:
 def gsdf_energy_visibility(e: int, psi_ptr: int, g_ptr: int, T_ptr: int, nu_ptr: int) -> int:
     return load_library().gsdf_energy_visibility(C.c_void_p(e), C.c_void_p(psi_ptr or None), C.c_void_p(g_ptr or None),
                                                  C.c_void_p(T_ptr), C.c_void_p(nu_ptr or None))
+
+
+def gsdf_energy_ba_step(e: int, psi_ptr: int, g_ptr: int, rho_ptr: int, T_ptr: int, nu_ptr: int, lambda_geo: float,
+                        damping: float, flags: int, stats_ptr: int = 0) -> int:
+    v = lambda x: C.c_void_p(x or None)  # noqa: E731
+    return load_library().gsdf_energy_ba_step(C.c_void_p(e), v(psi_ptr), v(g_ptr), v(rho_ptr), v(T_ptr), v(nu_ptr),
+                                              lambda_geo, damping, flags, v(stats_ptr))
 
 
 def gsdf_energy_eval(e: int, psi_ptr: int, g_ptr: int, rho_ptr: int, T_ptr: int, nu_ptr: int, lambda_geo: float,
@@ -499,6 +510,18 @@ class Energy:
                                 _ptr(grad_scale), E.data_ptr(), _ptr(dpsi), _ptr(dg), _ptr(drho), dT.data_ptr(),
                                 dxi.data_ptr()), "gsdf_energy_eval")
         return E, dpsi, dg, drho, dT, dxi
+
+
+def _energy_ba_step(self, psi, g, rho, poses, nu, lambda_geo: float, damping: float, flags: int, stats=None):
+    """One photometric bundle-adjustment iteration (gsdf_energy_ba_step): psi (n,) float32 and poses
+    (F, 4, 4) float64 are updated in place as flags select; rho (n, 3) float32 receives the mean
+    colours; stats: None or a (F, TRACK_STATS_BYTES) uint8 CUDA tensor."""
+    self._stream()
+    _check(gsdf_energy_ba_step(self.e, _ptr(psi), _ptr(g), _ptr(rho), poses.data_ptr(), _ptr(nu), lambda_geo,
+                               damping, flags, _ptr(stats)), "gsdf_energy_ba_step")
+
+
+Energy.ba_step = _energy_ba_step
 
 
 def _voxel_energy_function():
