@@ -1156,3 +1156,203 @@ size_t orc_points(int64_t n, const int32_t* m, const double* psi, const double* 
     }
     return count;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* layered marching cubes (Sec. 4.3)                                                           */
+/* ------------------------------------------------------------------------------------------ */
+
+/* corners of edge e: the corner with the edge's axis bit 0, and the one with it 1 */
+static void orc_edge_corners(int e, int* a, int* b) {
+    const int axis = e >> 2, k = e & 3;
+    int lo = 0;
+    if (axis == 0) lo = ((k & 1) << 1) | ((k >> 1) << 2);  /* dy = k&1, dz = k>>1 */
+    if (axis == 1) lo = (k & 1) | ((k >> 1) << 2);         /* dx = k&1, dz = k>>1 */
+    if (axis == 2) lo = (k & 1) | ((k >> 1) << 1);         /* dx = k&1, dy = k>>1 */
+    *a = lo;
+    *b = lo | (1 << axis);
+}
+
+/* triangles (edge triples) of case `inside` (bit c = corner c inside); returns their number */
+static int orc_mc_case(int inside, int tri[][3]) {
+    int nb[12][2], deg[12];
+    for (int e = 0; e < 12; ++e) deg[e] = 0;
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int side = 0; side < 2; ++side) {
+            /* the face's 4 corners in cyclic order and the edge between consecutive ones */
+            const int u = (axis + 1) % 3, w = (axis + 2) % 3;
+            int cs[4], es[4];
+            const int du[4] = {0, 1, 1, 0}, dw[4] = {0, 0, 1, 1};
+            for (int q = 0; q < 4; ++q) cs[q] = (side << axis) | (du[q] << u) | (dw[q] << w);
+            for (int q = 0; q < 4; ++q) {
+                const int c0 = cs[q], c1 = cs[(q + 1) % 4];
+                for (int e = 0; e < 12; ++e) {
+                    int a, b;
+                    orc_edge_corners(e, &a, &b);
+                    if ((a == c0 && b == c1) || (a == c1 && b == c0)) es[q] = e;
+                }
+            }
+            int cross[4], nc = 0;
+            for (int q = 0; q < 4; ++q) {
+                const int i0 = (inside >> cs[q]) & 1, i1 = (inside >> cs[(q + 1) % 4]) & 1;
+                if (i0 != i1) cross[nc++] = q;
+            }
+            int pairs[2][2], np = 0;
+            if (nc == 2) {
+                pairs[0][0] = es[cross[0]];
+                pairs[0][1] = es[cross[1]];
+                np = 1;
+            } else if (nc == 4) {
+                /* inside corners on a diagonal: each is cut off by joining its two edges
+                 * (edge q joins corners q and q+1, so corner q lies between edges q-1 and q) */
+                for (int q = 0; q < 4; ++q) {
+                    if ((inside >> cs[q]) & 1) {
+                        pairs[np][0] = es[(q + 3) % 4];
+                        pairs[np][1] = es[q];
+                        ++np;
+                    }
+                }
+            }
+            for (int p = 0; p < np; ++p) {
+                const int e0 = pairs[p][0], e1 = pairs[p][1];
+                nb[e0][deg[e0]++] = e1;
+                nb[e1][deg[e1]++] = e0;
+            }
+        }
+    }
+    int used[12] = {0}, nt = 0;
+    for (int start = 0; start < 12; ++start) {
+        if (deg[start] != 2 || used[start]) continue;
+        int loop[12], len = 0, prev = -1, cur = start;
+        int next = nb[start][0] < nb[start][1] ? nb[start][0] : nb[start][1];
+        for (;;) {
+            loop[len++] = cur;
+            used[cur] = 1;
+            if (prev >= 0) next = nb[cur][0] == prev ? nb[cur][1] : nb[cur][0];
+            prev = cur;
+            cur = next;
+            if (cur == start) break;
+        }
+        for (int k = 1; k + 1 < len; ++k) {
+            tri[nt][0] = loop[0];
+            tri[nt][1] = loop[k];
+            tri[nt][2] = loop[k + 1];
+            ++nt;
+        }
+    }
+    return nt;
+}
+
+typedef struct {
+    int32_t m[3];
+    double psi;
+} orc_zvox;
+
+static int orc_cmp_zvox(const void* pa, const void* pb) {
+    const orc_zvox* a = (const orc_zvox*)pa;
+    const orc_zvox* b = (const orc_zvox*)pb;
+    for (int k = 2; k >= 0; --k) {
+        if (a->m[k] < b->m[k]) return -1;
+        if (a->m[k] > b->m[k]) return 1;
+    }
+    return 0;
+}
+
+size_t orc_marching_cubes(int64_t n, const int32_t* m, const double* psi, float voxel_size, orc_triangle* out,
+                          size_t cap) {
+    if (n <= 0) return 0;
+    const double vs = (double)voxel_size;
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) lo[k] = hi[k] = m[k];
+    for (int64_t j = 1; j < n; ++j)
+        for (int k = 0; k < 3; ++k) {
+            if (m[3 * j + k] < lo[k]) lo[k] = m[3 * j + k];
+            if (m[3 * j + k] > hi[k]) hi[k] = m[3 * j + k];
+        }
+    orc_zvox* zs = (orc_zvox*)malloc(sizeof(orc_zvox) * (size_t)n);
+    const size_t nx = (size_t)(hi[0] - lo[0] + 1), ny = (size_t)(hi[1] - lo[1] + 1);
+    double* layer[2];
+    unsigned char* have[2];
+    layer[0] = (double*)malloc(sizeof(double) * nx * ny);
+    layer[1] = (double*)malloc(sizeof(double) * nx * ny);
+    have[0] = (unsigned char*)calloc(nx * ny, 1);
+    have[1] = (unsigned char*)calloc(nx * ny, 1);
+    if (!zs || !layer[0] || !layer[1] || !have[0] || !have[1]) {
+        free(zs);
+        free(layer[0]);
+        free(layer[1]);
+        free(have[0]);
+        free(have[1]);
+        return 0;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        for (int k = 0; k < 3; ++k) zs[j].m[k] = m[3 * j + k];
+        zs[j].psi = psi[j];
+    }
+    qsort(zs, (size_t)n, sizeof(orc_zvox), orc_cmp_zvox);
+    int table[256][12][3], counts[256];
+    for (int c = 0; c < 256; ++c) counts[c] = orc_mc_case(c, table[c]);
+    /* two z-layers of the bounding box at a time: layer 1 holds z, layer 0 holds z - 1 */
+    int64_t pos = 0;
+    size_t count = 0;
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+        double* tl = layer[0];
+        unsigned char* th = have[0];
+        layer[0] = layer[1];
+        have[0] = have[1];
+        layer[1] = tl;
+        have[1] = th;
+        memset(have[1], 0, nx * ny);
+        while (pos < n && zs[pos].m[2] == z) {
+            const size_t at = (size_t)(zs[pos].m[1] - lo[1]) * nx + (size_t)(zs[pos].m[0] - lo[0]);
+            layer[1][at] = zs[pos].psi;
+            have[1][at] = 1;
+            ++pos;
+        }
+        if (z == lo[2]) continue;
+        /* cubes with lowest corner in layer z - 1 */
+        for (size_t y = 0; y + 1 < ny; ++y) {
+            for (size_t x = 0; x + 1 < nx; ++x) {
+                double cp[8];
+                int ok = 1, inside = 0;
+                for (int c = 0; c < 8; ++c) {
+                    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+                    const size_t at = (y + dy) * nx + (x + dx);
+                    if (!have[dz][at]) {
+                        ok = 0;
+                        break;
+                    }
+                    cp[c] = layer[dz][at];
+                    if (cp[c] > 0.0) inside |= 1 << c;
+                }
+                if (!ok || counts[inside] == 0) continue;
+                const int32_t mc[3] = {lo[0] + (int32_t)x, lo[1] + (int32_t)y, z - 1};
+                for (int t = 0; t < counts[inside]; ++t) {
+                    if (count < cap) {
+                        orc_triangle* o = out + count;
+                        o->m[0] = mc[0];
+                        o->m[1] = mc[1];
+                        o->m[2] = mc[2];
+                        o->edges = table[inside][t][0] | (table[inside][t][1] << 4) | (table[inside][t][2] << 8);
+                        for (int k = 0; k < 3; ++k) {
+                            int a, b;
+                            orc_edge_corners(table[inside][t][k], &a, &b);
+                            const double tt = cp[a] / (cp[a] - cp[b]);
+                            for (int d = 0; d < 3; ++d) {
+                                const double va = vs * (double)(mc[d] + ((a >> d) & 1));
+                                const double vb = vs * (double)(mc[d] + ((b >> d) & 1));
+                                o->v[3 * k + d] = va + tt * (vb - va);
+                            }
+                        }
+                    }
+                    ++count;
+                }
+            }
+        }
+    }
+    free(zs);
+    free(layer[0]);
+    free(layer[1]);
+    free(have[0]);
+    free(have[1]);
+    return count;
+}

@@ -185,6 +185,28 @@ typedef struct {
 size_t orc_points(int64_t n, const int32_t* m, const double* psi, const double* g, float voxel_size, int level,
                   orc_point* out, size_t cap);
 
+/* ---------------------------------------------------------------------------------------------
+ * Layered marching cubes (Sec. 4.3): the axis-aligned bounding box of the voxel list is swept two
+ * z-layers at a time; every cube whose 8 corners (voxel centres m + {0,1}^3) are in the list gives
+ * the triangles of its case.  A corner is inside when psi > 0; an edge with one inside corner
+ * carries the vertex v_a + t (v_b - v_a), t = psi_a / (psi_a - psi_b).  Triangulation rule (any
+ * marching-cubes table is such a rule; this one is stated so it can be reproduced): on each
+ * face the crossing edges are joined in pairs -- a face with two crossings joins them, a face with
+ * four (two inside corners on a diagonal) joins, for each inside corner, its two edges -- the
+ * joins form closed loops through the crossing edges, each loop is walked from its smallest edge
+ * id toward the smaller of that edge's two neighbours, and fanned from its first edge.
+ * Edge ids: x-edges 0..3 (k = dy + 2 dz), y-edges 4..7 (k = dx + 2 dz), z-edges 8..11
+ * (k = dx + 2 dy); corner index dx + 2 dy + 4 dz.  Cubes in z, y, x order; the triangles of a cube
+ * in loop order.  Returns the number of triangles (writes at most cap). */
+typedef struct {
+    int32_t m[3];   /* the cube's lowest corner */
+    int32_t edges;  /* e0 | e1 << 4 | e2 << 8 */
+    double v[9];    /* the three vertices */
+} orc_triangle;
+
+size_t orc_marching_cubes(int64_t n, const int32_t* m, const double* psi, float voxel_size, orc_triangle* out,
+                          size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

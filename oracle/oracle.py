@@ -95,6 +95,8 @@ def lib():
                                   C.c_int, P(Intrinsics), P(C.c_double), P(P(C.c_float)), P(P(C.c_float)),
                                   P(C.c_uint8), C.c_double, C.c_double, C.c_int, P(TrackStats), P(C.c_double),
                                   P(C.c_double)]
+        L.orc_marching_cubes.restype = C.c_size_t
+        L.orc_marching_cubes.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), C.c_float, C.c_void_p, C.c_size_t]
         L.orc_points.restype = C.c_size_t
         L.orc_points.argtypes = [C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double), C.c_float, C.c_int,
                                  C.c_void_p, C.c_size_t]
@@ -359,3 +361,19 @@ def ba_step(m, psi, g, voxel_size, cam, poses, rgbs, depths, nu, lambda_geo, dam
     if rc != 0:
         raise MemoryError("orc_ba_step failed")
     return psi, rho, [P[i].reshape(4, 4).copy() for i in range(F)], list(st), hp, hb
+
+
+TRIANGLE_DTYPE = np.dtype([("m", np.int32, 3), ("edges", np.int32), ("v", np.float64, 9)], align=True)
+
+
+def marching_cubes(m, psi, voxel_size):
+    """Layered marching cubes over a voxel list (every listed voxel counts as observed).
+    Structured array (m, edges, v) of triangles."""
+    m = np.ascontiguousarray(m, np.int32)
+    psi = np.ascontiguousarray(psi, np.float64)
+    n = len(psi)
+    k = lib().orc_marching_cubes(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), voxel_size, None, 0)
+    out = np.zeros(max(k, 1), TRIANGLE_DTYPE)
+    k2 = lib().orc_marching_cubes(n, _ptr(m, C.c_int32), _ptr(psi, C.c_double), voxel_size, out.ctypes.data, k)
+    assert k2 == k
+    return out[:k]
