@@ -158,6 +158,15 @@ typedef struct {
     float n[3];
 } gsdf_point;
 
+/* One triangle of the marching-cubes mesh, as returned by gsdf_extract_mesh (52 bytes): the cube's
+ * lowest corner m, the cube edges its vertices lie on (e0 | e1 << 4 | e2 << 8, numbering in
+ * gsdf_extract_mesh) and the three vertices. */
+typedef struct {
+    int32_t m[3];
+    int32_t edges;
+    float v[9];
+} gsdf_triangle;
+
 typedef struct gsdf_handle gsdf_handle;
 
 /* Create a map on the current CUDA device.  Allocates the table, the voxel payload (zeroed:
@@ -240,6 +249,22 @@ gsdf_status gsdf_load_voxels(gsdf_handle* h, const gsdf_voxel* host_in, size_t n
  * GSDF_ERR_CAPACITY is returned).  Synchronous; may allocate temporary device memory. */
 gsdf_status gsdf_extract_points(gsdf_handle* h, int32_t level, gsdf_point* host_out, size_t capacity,
                                 size_t* count_out);
+
+/* Marching-cubes mesh of the map (Sec. 4.3, the mesh the paper's layered marching cubes extracts):
+ * every cube whose 8 corners m + {0,1}^3 (voxel centres) are observed (W > 0) gives the triangles
+ * of its case.  A corner is inside when psi > 0; an edge between an inside and an outside corner
+ * carries the vertex v_a + t (v_b - v_a), t = psi_a / (psi_a - psi_b).  Corner index c = dx + 2 dy
+ * + 4 dz; edge ids: x-edges 0..3 (k = dy + 2 dz), y-edges 4..7 (k = dx + 2 dz), z-edges 8..11
+ * (k = dx + 2 dy).  Triangulation rule: on each cube face the crossing edges are joined in pairs
+ * (two crossings: joined; four, i.e. two inside corners on a diagonal: each inside corner's two
+ * edges joined, which separates the inside corners), the joins close into loops, each loop is
+ * walked from its smallest edge id toward the smaller of its two neighbours and fanned from its
+ * first edge.  The rule depends only on a face's own corners, so neighbouring cubes agree and the
+ * mesh of a closed surface is closed.  The paper sweeps a bounding box two z-layers at a time to
+ * bound a CPU's memory; the library visits the same cubes directly through the map.  Order: the
+ * voxel order of gsdf_extract_voxels (by lowest corner), then the case's triangle order.
+ * Capacity semantics as gsdf_extract_voxels.  Synchronous; may allocate temporary device memory. */
+gsdf_status gsdf_extract_mesh(gsdf_handle* h, gsdf_triangle* host_out, size_t capacity, size_t* count_out);
 
 /* Number of allocated hash blocks (dense: number of 512-voxel chunks).  Synchronous. */
 gsdf_status gsdf_num_blocks(gsdf_handle* h, int64_t* n_out);

@@ -1,5 +1,6 @@
 // Extraction of every voxel with W > 0 in a canonical order, the oriented point cloud of Sec. 4.3
-// (and its 2x2x2 Taylor upsampling) in the same order, and checkpoint loading.
+// (and its 2x2x2 Taylor upsampling) and the marching-cubes mesh in the same order, and checkpoint
+// loading.
 //
 // Hashed maps: the occupied slots' block keys are collected, sorted (bitonic sort in global
 // memory; keys are unique, so the order is total), counted, prefix-summed, and each block's
@@ -529,6 +530,289 @@ cudaError_t extract_points(const DenseMap* dm, const HashMap* hm, const HashMap1
     *out_dev = out.release();
     *n_out = total;
     return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------------
+// marching cubes (Sec. 4.3)
+// ------------------------------------------------------------------------------------------
+
+// The triangulation of each of the 256 cube cases, generated at compile time from the rule stated
+// in include/gsdf.h (gsdf_extract_mesh): per face, crossing edges joined in pairs (an ambiguous
+// face separates its inside corners), the joins closed into loops walked from the smallest edge
+// id toward its smaller neighbour, each loop fanned from its first edge.
+struct McTable {
+    unsigned char count[256];
+    unsigned char tri[256][12][3];
+};
+
+__host__ __device__ constexpr int mc_edge_lo(int e) {  // corner of edge e with the edge's axis bit clear
+    const int axis = e >> 2, k = e & 3;
+    return axis == 0 ? (((k & 1) << 1) | ((k >> 1) << 2)) : axis == 1 ? ((k & 1) | ((k >> 1) << 2)) : ((k & 1) | ((k >> 1) << 1));
+}
+
+constexpr int mc_edge_between(int c0, int c1) {  // edge joining two corners that differ in one bit
+    const int diff = c0 ^ c1;
+    const int axis = diff == 1 ? 0 : diff == 2 ? 1 : 2;
+    const int lo = c0 & ~diff;
+    const int k = axis == 0 ? (((lo >> 1) & 1) | (((lo >> 2) & 1) << 1))
+                            : axis == 1 ? ((lo & 1) | (((lo >> 2) & 1) << 1)) : ((lo & 1) | (((lo >> 1) & 1) << 1));
+    return 4 * axis + k;
+}
+
+constexpr McTable make_mc_table() {
+    McTable t{};
+    for (int cs = 0; cs < 256; ++cs) {
+        int nb[12][2] = {};
+        int deg[12] = {};
+        for (int axis = 0; axis < 3; ++axis) {
+            for (int side = 0; side < 2; ++side) {
+                const int u = (axis + 1) % 3, w = (axis + 2) % 3;
+                const int du[4] = {0, 1, 1, 0}, dw[4] = {0, 0, 1, 1};
+                int corner[4] = {}, edge[4] = {};
+                for (int q = 0; q < 4; ++q) corner[q] = (side << axis) | (du[q] << u) | (dw[q] << w);
+                for (int q = 0; q < 4; ++q) edge[q] = mc_edge_between(corner[q], corner[(q + 1) % 4]);
+                int crossings = 0, first = -1, second = -1;
+                for (int q = 0; q < 4; ++q) {
+                    if (((cs >> corner[q]) & 1) != ((cs >> corner[(q + 1) % 4]) & 1)) {
+                        ++crossings;
+                        if (first < 0)
+                            first = edge[q];
+                        else
+                            second = edge[q];
+                    }
+                }
+                int join[2][2] = {};
+                int nj = 0;
+                if (crossings == 2) {
+                    join[0][0] = first;
+                    join[0][1] = second;
+                    nj = 1;
+                } else if (crossings == 4) {
+                    for (int q = 0; q < 4; ++q)
+                        if ((cs >> corner[q]) & 1) {  // cut off the inside corner q
+                            join[nj][0] = edge[(q + 3) % 4];
+                            join[nj][1] = edge[q];
+                            ++nj;
+                        }
+                }
+                for (int j = 0; j < nj; ++j) {
+                    nb[join[j][0]][deg[join[j][0]]++] = join[j][1];
+                    nb[join[j][1]][deg[join[j][1]]++] = join[j][0];
+                }
+            }
+        }
+        bool used[12] = {};
+        int nt = 0;
+        for (int start = 0; start < 12; ++start) {
+            if (deg[start] != 2 || used[start]) continue;
+            int loop[12] = {};
+            int len = 0, prev = -1, cur = start;
+            int next = nb[start][0] < nb[start][1] ? nb[start][0] : nb[start][1];
+            while (true) {
+                loop[len++] = cur;
+                used[cur] = true;
+                if (prev >= 0) next = nb[cur][0] == prev ? nb[cur][1] : nb[cur][0];
+                prev = cur;
+                cur = next;
+                if (cur == start) break;
+            }
+            for (int k = 1; k + 1 < len; ++k) {
+                t.tri[cs][nt][0] = (unsigned char)loop[0];
+                t.tri[cs][nt][1] = (unsigned char)loop[k];
+                t.tri[cs][nt][2] = (unsigned char)loop[k + 1];
+                ++nt;
+            }
+        }
+        t.count[cs] = (unsigned char)nt;
+    }
+    return t;
+}
+
+__constant__ McTable c_mc = make_mc_table();
+
+// psi of the 8 corners of the cube with lowest corner m; false unless all are observed
+template <class Map>
+__device__ __forceinline__ bool cube_corners(const Map& map, const int m[3], float psi[8]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const long long idx = map.find(m[0] + (c & 1), m[1] + ((c >> 1) & 1), m[2] + ((c >> 2) & 1));
+        if (idx < 0) return false;
+        float g0, g1, g2;
+        if (!map.voxel(idx, psi[c], g0, g1, g2)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ int cube_case(const float psi[8]) {
+    int cs = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cs |= (psi[c] > 0.0f ? 1 : 0) << c;
+    return cs;
+}
+
+struct MeshSrc {
+    const unsigned long long* sorted;
+    const long long* base;
+    long long dense_voxels;
+    int dx, dy, ox, oy, oz;
+    float vs;
+};
+
+__device__ __forceinline__ bool mesh_cube(const MeshSrc& s, long long c, int t, int m[3]) {
+    const long long b0 = s.base[c];
+    if (b0 < 0) return false;
+    if (s.sorted) {
+        int b[3];
+        unpack_block(s.sorted[c], b);
+        m[0] = b[0] * 8 + (t & 7);
+        m[1] = b[1] * 8 + ((t >> 3) & 7);
+        m[2] = b[2] * 8 + (t >> 6);
+        return true;
+    }
+    const long long i = b0 + t;
+    if (i >= s.dense_voxels) return false;
+    m[0] = s.ox + (int)(i % s.dx);
+    m[1] = s.oy + (int)((i / s.dx) % s.dy);
+    m[2] = s.oz + (int)(i / ((long long)s.dx * s.dy));
+    return true;
+}
+
+template <class Map>
+__global__ void mesh_count_kernel(Map map, MeshSrc s, long long n_chunks, unsigned int* counts) {
+    __shared__ unsigned int cnt;
+    for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        int m[3];
+        float psi[8];
+        unsigned k = 0;
+        if (mesh_cube(s, c, threadIdx.x, m) && cube_corners(map, m, psi)) k = c_mc.count[cube_case(psi)];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+        if ((threadIdx.x & 31) == 0 && k) atomicAdd(&cnt, k);
+        __syncthreads();
+        if (threadIdx.x == 0) counts[c] = cnt;
+        __syncthreads();
+    }
+}
+
+template <class Map>
+__global__ void mesh_write_kernel(Map map, MeshSrc s, long long n_chunks, const long long* __restrict__ offsets,
+                                  gsdf_triangle* out) {
+    __shared__ unsigned int warp_off[kBlockVoxels / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        int m[3];
+        float psi[8];
+        int cs = 0;
+        unsigned k = 0;
+        if (mesh_cube(s, c, threadIdx.x, m) && cube_corners(map, m, psi)) {
+            cs = cube_case(psi);
+            k = c_mc.count[cs];
+        }
+        unsigned incl = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_off[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned run = 0;
+            for (int w = 0; w < kBlockVoxels / 32; ++w) {
+                const unsigned x = warp_off[w];
+                warp_off[w] = run;
+                run += x;
+            }
+        }
+        __syncthreads();
+        long long pos = offsets[c] + warp_off[warp] + incl - k;
+        for (unsigned q = 0; q < k; ++q) {
+            gsdf_triangle o;
+            o.m[0] = m[0];
+            o.m[1] = m[1];
+            o.m[2] = m[2];
+            o.edges = 0;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const int e = c_mc.tri[cs][q][v];
+                o.edges |= e << (4 * v);
+                const int a = mc_edge_lo(e), b = a | (1 << (e >> 2));
+                const float t = psi[a] / (psi[a] - psi[b]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float va = s.vs * (float)(m[d] + ((a >> d) & 1));
+                    const float vb = s.vs * (float)(m[d] + ((b >> d) & 1));
+                    o.v[3 * v + d] = va + t * (vb - va);
+                }
+            }
+            out[pos++] = o;
+        }
+        __syncthreads();
+    }
+}
+
+template <class Map>
+static cudaError_t mesh_passes(const Map& map, const MeshSrc& src, long long n_chunks, unsigned cgrid,
+                               unsigned int* counts, long long* offsets, cudaStream_t st, gsdf_triangle** out_dev,
+                               long long* n_out) {
+    mesh_count_kernel<Map><<<cgrid, kBlockVoxels, 0, st>>>(map, src, n_chunks, counts);
+    GSDF_CK(cudaGetLastError());
+    scan_kernel<<<1, 1024, 0, st>>>(counts, n_chunks, offsets);
+    GSDF_CK(cudaGetLastError());
+    long long total = 0;
+    GSDF_CK(cudaMemcpyAsync(&total, offsets + n_chunks, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    GSDF_CK(cudaStreamSynchronize(st));
+    if (total == 0) return cudaSuccess;
+    DevBuf<gsdf_triangle> out;
+    GSDF_CK(out.alloc((size_t)total));
+    mesh_write_kernel<Map><<<cgrid, kBlockVoxels, 0, st>>>(map, src, n_chunks, offsets, out.p);
+    GSDF_CK(cudaGetLastError());
+    GSDF_CK(cudaStreamSynchronize(st));
+    *out_dev = out.release();
+    *n_out = total;
+    return cudaSuccess;
+}
+
+cudaError_t extract_mesh(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
+                         float voxel_size, cudaStream_t st, int num_sms, gsdf_triangle** out_dev, long long* n_out) {
+    *out_dev = nullptr;
+    *n_out = 0;
+    const unsigned grid = (unsigned)(num_sms * 8);
+    DevBuf<unsigned long long> keys;
+    long long n_chunks = 0, dense_voxels = 0;
+    if (hm) {
+        GSDF_CK(sorted_block_keys(*hm, n_slots, st, grid, keys, &n_chunks));
+    } else {
+        dense_voxels = (long long)dm->dims[0] * dm->dims[1] * dm->dims[2];
+        n_chunks = (dense_voxels + kBlockVoxels - 1) / kBlockVoxels;
+    }
+    if (n_chunks == 0) return cudaSuccess;
+    DevBuf<long long> base, offsets;
+    DevBuf<unsigned int> counts;
+    GSDF_CK(base.alloc((size_t)n_chunks));
+    GSDF_CK(counts.alloc((size_t)n_chunks));
+    GSDF_CK(offsets.alloc((size_t)n_chunks + 1));
+    const HashMap hmv = hm ? *hm : HashMap{};
+    const float* W = h16 ? h16->W : (hm ? hm->W : dm->W);
+    const unsigned long long* sorted = hm ? keys.p : nullptr;
+    const unsigned cgrid = (unsigned)(n_chunks < (long long)num_sms * 16 ? n_chunks : (long long)num_sms * 16);
+    chunk_count_kernel<<<cgrid, kBlockVoxels, 0, st>>>(hmv, sorted, n_chunks, dense_voxels, W, base.p, counts.p);
+    GSDF_CK(cudaGetLastError());
+    MeshSrc src{};
+    src.sorted = sorted;
+    src.base = base.p;
+    src.dense_voxels = dense_voxels;
+    src.dx = dm ? dm->dims[0] : 0;
+    src.dy = dm ? dm->dims[1] : 0;
+    src.ox = dm ? dm->origin[0] : 0;
+    src.oy = dm ? dm->origin[1] : 0;
+    src.oz = dm ? dm->origin[2] : 0;
+    src.vs = voxel_size;
+    if (h16) return mesh_passes(*h16, src, n_chunks, cgrid, counts.p, offsets.p, st, out_dev, n_out);
+    if (hm) return mesh_passes(*hm, src, n_chunks, cgrid, counts.p, offsets.p, st, out_dev, n_out);
+    return mesh_passes(*dm, src, n_chunks, cgrid, counts.p, offsets.p, st, out_dev, n_out);
 }
 
 cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, float trunc,

@@ -341,6 +341,25 @@ gsdf_status gsdf_extract_points(gsdf_handle* h, int32_t level, gsdf_point* host_
     return (size_t)n > capacity ? GSDF_ERR_CAPACITY : GSDF_OK;
 }
 
+gsdf_status gsdf_extract_mesh(gsdf_handle* h, gsdf_triangle* host_out, size_t capacity, size_t* count_out) {
+    if (!h || !count_out || (capacity > 0 && !host_out)) return GSDF_ERR_INVALID_ARG;
+    gsdf_triangle* dev = nullptr;
+    long long n = 0;
+    cudaError_t e = extract_mesh(h->hashed ? nullptr : &h->dm, h->hashed ? &h->hm : nullptr, h->fp16 ? &h->hm16 : nullptr,
+                                 h->hashed ? h->cfg.hash_slots : 0, h->cfg.voxel_size, h->stream, h->num_sms, &dev, &n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    *count_out = (size_t)n;
+    const size_t k = (size_t)n < capacity ? (size_t)n : capacity;
+    if (k > 0) e = cudaMemcpyAsync(host_out, dev, sizeof(gsdf_triangle) * k, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (size_t)n > capacity ? GSDF_ERR_CAPACITY : GSDF_OK;
+}
+
 gsdf_status gsdf_load_voxels(gsdf_handle* h, const gsdf_voxel* host_in, size_t n) {
     if (!h || (n > 0 && !host_in)) return GSDF_ERR_INVALID_ARG;
     for (size_t i = 0; i < n; ++i)

@@ -327,6 +327,8 @@ cudaError_t extract_voxels(const DenseMap* dm, const HashMap* hm, const HashMap1
 cudaError_t extract_points(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
                            float voxel_size, int level, cudaStream_t st, int num_sms, gsdf_point** out_dev,
                            long long* n_out);
+cudaError_t extract_mesh(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, long long n_slots,
+                         float voxel_size, cudaStream_t st, int num_sms, gsdf_triangle** out_dev, long long* n_out);
 cudaError_t load_voxels(const DenseMap* dm, const HashMap* hm, const HashMap16* h16, float trunc,
                         const gsdf_voxel* in_dev, long long n, int* err, unsigned int* n_blocks, cudaStream_t st,
                         int num_sms);

@@ -69,6 +69,13 @@ class gsdf_point(C.Structure):
 
 
 POINT_DTYPE = np.dtype([("m", "<i4", 3), ("sub", "<i4"), ("p", "<f4", 3), ("n", "<f4", 3)])
+
+
+class gsdf_triangle(C.Structure):
+    _fields_ = [("m", C.c_int32 * 3), ("edges", C.c_int32), ("v", C.c_float * 9)]
+
+
+TRIANGLE_DTYPE = np.dtype([("m", "<i4", 3), ("edges", "<i4"), ("v", "<f4", 9)])
 TRACK_STATS_BYTES = C.sizeof(gsdf_track_stats)
 INTEGRATE_STATS_BYTES = C.sizeof(gsdf_integrate_stats)
 
@@ -86,6 +93,7 @@ _SIGS = {
     "gsdf_load_voxels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "gsdf_num_blocks": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "gsdf_extract_points": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
+    "gsdf_extract_mesh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
     "gsdf_sync": (C.c_int, [C.c_void_p]),
     "gsdf_status_string": (C.c_char_p, [C.c_int]),
     "gsdf_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, _P(C.c_void_p)]),
@@ -194,6 +202,13 @@ def gsdf_extract_points(h: int, level: int, out: np.ndarray | None, capacity: in
     n = C.c_size_t()
     ptr = out.ctypes.data if out is not None else None
     st = load_library().gsdf_extract_points(C.c_void_p(h), level, C.c_void_p(ptr), capacity, C.byref(n))
+    return st, n.value
+
+
+def gsdf_extract_mesh(h: int, out: np.ndarray | None, capacity: int):
+    n = C.c_size_t()
+    ptr = out.ctypes.data if out is not None else None
+    st = load_library().gsdf_extract_mesh(C.c_void_p(h), C.c_void_p(ptr), capacity, C.byref(n))
     return st, n.value
 
 
@@ -386,6 +401,19 @@ class Map:
         if st == GSDF_ERR_CAPACITY:
             return self.extract_points(level, n)
         _check(st, "gsdf_extract_points")
+        return out[:n]
+
+    def extract_mesh(self, capacity: int | None = None) -> np.ndarray:
+        """Marching-cubes triangles (m, edges, v) of the map; one library call when capacity suffices."""
+        if capacity is None:
+            st, capacity = gsdf_extract_mesh(self.h, None, 0)
+            if st not in (GSDF_OK, GSDF_ERR_CAPACITY):
+                _check(st, "gsdf_extract_mesh")
+        out = np.zeros(capacity, TRIANGLE_DTYPE)
+        st, n = gsdf_extract_mesh(self.h, out, capacity)
+        if st == GSDF_ERR_CAPACITY:
+            return self.extract_mesh(n)
+        _check(st, "gsdf_extract_mesh")
         return out[:n]
 
     def load(self, vox: np.ndarray):

@@ -80,6 +80,7 @@ int main(void) {
   printf("%zu %zu %zu\n", offsetof(gsdf_config, hash_slots), offsetof(gsdf_track_stats, xi),
          offsetof(gsdf_voxel, w));
   printf("%zu %zu %zu\n", sizeof(gsdf_point), offsetof(gsdf_point, p), offsetof(gsdf_point, n));
+  printf("%zu %zu\n", sizeof(gsdf_triangle), offsetof(gsdf_triangle, v));
   return 0;
 }
 ''')
@@ -89,7 +90,9 @@ int main(void) {
     assert vals == [C.sizeof(G.gsdf_config), C.sizeof(G.gsdf_intrinsics), C.sizeof(G.gsdf_track_stats),
                     C.sizeof(G.gsdf_integrate_stats), C.sizeof(G.gsdf_voxel), G.gsdf_config.damping.offset,
                     G.gsdf_config.hash_slots.offset, G.gsdf_track_stats.xi.offset, G.gsdf_voxel.w.offset,
-                    C.sizeof(G.gsdf_point), G.gsdf_point.p.offset, G.gsdf_point.n.offset]
+                    C.sizeof(G.gsdf_point), G.gsdf_point.p.offset, G.gsdf_point.n.offset,
+                    C.sizeof(G.gsdf_triangle), G.gsdf_triangle.v.offset]
+    assert G.TRIANGLE_DTYPE.itemsize == C.sizeof(G.gsdf_triangle) == 52
     assert G.VOXEL_DTYPE.itemsize == C.sizeof(G.gsdf_voxel) == 32
     assert G.POINT_DTYPE.itemsize == C.sizeof(G.gsdf_point) == 40
     assert G.POINT_DTYPE.fields["p"][1] == G.gsdf_point.p.offset and G.POINT_DTYPE.fields["n"][1] == G.gsdf_point.n.offset
