@@ -204,9 +204,10 @@ gsdf_status gsdf_integrate(gsdf_handle* h, const float* depth_dev, const gsdf_in
  * For every valid pixel, P = R p + t, the nearest voxel m = floor(P / v_s + 1/2) is looked up;
  * if it exists with W > 0 and g != 0, r = psi + ghat.(P - v_s m), J = (P x ghat, ghat),
  * w = Huber(r).  The normal equations are reduced on the device, (H + lambda I) xi = -b is
- * solved by Cholesky in FP64 and T_wc_dev is replaced by exp(xi^) T_wc_dev, all without
- * a host round trip.  If fewer than 6 pixels are usable or a pivot is <= 1e-12 max diag(H),
- * the pose is left unchanged and stats.status = GSDF_ERR_DEGENERATE.
+ * solved in FP64 (lambda = damping * trace(H) / 6) and T_wc_dev is replaced by
+ * exp(xi^) T_wc_dev, all without a host round trip: the update of gsdf_gn_update.  If fewer
+ * than 6 pixels are usable or an LDL^T pivot of H + lambda I is <= 1e-12 times its largest
+ * diagonal entry, the pose is left unchanged and stats.status = GSDF_ERR_DEGENERATE.
  * T_wc_dev: 16 FP64 on the device, read and written.  stats_dev: optional (NULL allowed). */
 gsdf_status gsdf_track_step(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
                             double* T_wc_dev, gsdf_track_stats* stats_dev);
@@ -221,6 +222,26 @@ gsdf_status gsdf_track_step(gsdf_handle* h, const float* depth_dev, const gsdf_i
  * 1 <= n_iters <= 1024. */
 gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
                        double* T_wc_dev, int32_t n_iters, gsdf_track_stats* stats_dev);
+
+/* One damped Gauss-Newton update from given normal equations, for n independent systems on the
+ * device (Sec. 4.1: the increment that minimises the linearised tracking energy, applied to the
+ * pose as T <- exp(xi^) T; the last stage of every tracking step).  For system s:
+ *   Hb_dev[27 s ..]   FP64, read: the 21 upper-triangle terms of H, row-major (H00 H01 .. H05
+ *                     H11 .. H55), then the 6 of b -- the layout of gsdf_track_stats.H and .b;
+ *   n_valid_dev[s]    residual count; fewer than 6 makes the system degenerate;
+ *   damping           >= 0: solve (H + lambda I) xi = -b with lambda = damping * trace(H) / 6;
+ *   T_dev[16 s ..]    FP64 row-major 4x4 camera-to-world pose, read and replaced by
+ *                     exp(xi^) T (xi = (omega, upsilon), rotation first); unchanged if degenerate;
+ *   xi_dev[6 s ..]    NULL or written: the increment (zeros if degenerate);
+ *   status_dev[s]     NULL or written: GSDF_OK or GSDF_ERR_DEGENERATE.
+ * Degenerate: n_valid < 6, a diagonal entry of H + lambda I that is not positive, or an LDL^T
+ * pivot of H + lambda I at or below 1e-12 times its largest diagonal entry (as a Cholesky
+ * factorisation would test it).  All pointers are device memory owned by the caller; the call is
+ * asynchronous on cuda_stream (NULL: the legacy default stream) and allocates nothing.
+ * GSDF_ERR_INVALID_ARG: n < 0, damping negative or not finite, or a required pointer NULL with
+ * n > 0; GSDF_ERR_CUDA: the launch failed.  n = 0 does nothing. */
+gsdf_status gsdf_gn_update(int32_t n, const double* Hb_dev, const int64_t* n_valid_dev, double damping,
+                           double* T_dev, double* xi_dev, int32_t* status_dev, void* cuda_stream);
 
 /* Copy every voxel with W > 0 to host_out, ordered by block (lexicographic block coordinate)
  * and then local index for hashed grids, by linear index (x fastest) for dense grids.

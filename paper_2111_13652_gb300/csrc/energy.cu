@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(kEThreads) ba_geo_kernel(EnergyArgs a) {
 // One warp per keyframe: damped FP64 solve of its 6x6 system, left update exp(xi^) T, statistics;
 // clears the keyframe's accumulator and pair count for the next call.
 __global__ void __launch_bounds__(32) ba_solve_kernel(double* bacc, unsigned int* pair_count, double* T,
-                                                      double damping, int update, gsdf_track_stats* stats) {
+                                                      double lam_scale, int update, gsdf_track_stats* stats) {
     __shared__ double tot[32], xi[6], dT[16], Ts[16];
     const int i = blockIdx.x, lane = threadIdx.x;
     tot[lane] = bacc[32 * i + lane];
@@ -812,13 +812,12 @@ __global__ void __launch_bounds__(32) ba_solve_kernel(double* bacc, unsigned int
     const long long n_valid = (long long)(tot[28] + 0.5);
     bool ok = false;
     if (update) {
-        ok = solve6_warp(tot, damping, n_valid, xi);
-        if (ok) se3_exp_warp(xi, dT);
-        if (ok && lane < 12) {
-            const int r = lane >> 2, c = lane & 3;
-            double tn = (dT[4 * r] * Ts[c] + dT[4 * r + 1] * Ts[4 + c]) + dT[4 * r + 2] * Ts[8 + c];
-            if (c == 3) tn += dT[4 * r + 3];
-            T[16 * i + lane] = tn;
+        const double tr = ((tot[0] + tot[6]) + (tot[11] + tot[15])) + (tot[18] + tot[20]);
+        ok = solve6_warp(tot, tr, lam_scale, n_valid, xi);
+        if (ok) {
+            se3_exp_warp(xi, dT);
+            const double tn = compose_entry(dT, Ts);
+            if (lane < 12) T[16 * i + lane] = tn;
         }
     }
     if (stats) {
@@ -1229,7 +1228,7 @@ gsdf_status gsdf_energy_ba_step(gsdf_energy* e, float* psi_dev, const float* g_d
         const long long pneed = (npx + kEThreads - 1) / kEThreads;
         ba_geo_kernel<<<dim3(columns_for(e->ba_geo_blocks, e->F, pneed), e->F), kEThreads, 0, st>>>(a);
     }
-    ba_solve_kernel<<<e->F, 32, 0, st>>>(e->bacc, e->pair_count, T_dev, damping, (flags & GSDF_BA_POSES) ? 1 : 0,
+    ba_solve_kernel<<<e->F, 32, 0, st>>>(e->bacc, e->pair_count, T_dev, damping / 6.0, (flags & GSDF_BA_POSES) ? 1 : 0,
                                          stats_dev);
     if (e->n > 0)
         ba_psi_kernel<<<grid_for(e->n, e->vis_blocks), kEThreads, 0, st>>>(a, psi_dev, damping,

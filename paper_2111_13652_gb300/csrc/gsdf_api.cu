@@ -137,6 +137,7 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
     p.cos_max = cfg->cos_max_angle;
     p.band_half = (int)ceil((double)cfg->truncation / (double)p.half_vs - 1e-6);
     p.damping = cfg->damping;
+    p.lam_scale = cfg->damping / 6.0;
 
     cudaError_t e = cudaSuccess;
     float4* A = nullptr;

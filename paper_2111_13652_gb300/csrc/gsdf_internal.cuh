@@ -36,6 +36,7 @@ struct Params {
     float vs, inv_vs, trunc, eps, half_vs, huber, cos_max;
     int band_half;  // K = ceil(T / (v_s / 2))
     double damping;
+    double lam_scale;  // damping / 6: the Levenberg term is lam_scale * trace(H)
 };
 
 // Pose rounded once from FP64: camera->world (R, t) and world->camera (R^T, -R^T t).

@@ -37,48 +37,40 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
     finish_scene(sh, sc.accum, sc.counter, prm, T_wc, stats);
 }
 
-cudaError_t launch_track16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm, double* T_wc,
-                           gsdf_track_stats* stats, const Scratch& sc, int num_sms, cudaStream_t st) {
+static long long track_blocks(const Intr& K, const Scratch& sc, int num_sms) {
     const long long n_px = (long long)K.width * K.height;
     long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
     long long cap = (long long)kTrackBlocksPerSM * num_sms;
     if (cap > sc.max_track_blocks) cap = sc.max_track_blocks;
     if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    track_kernel<HashMap16><<<(unsigned)blocks, kTrackThreads, 0, st>>>(hm, depth, K, prm, T_wc, stats, sc);
+    return blocks < 1 ? 1 : blocks;
+}
+
+template <class Map, bool kTri>
+static cudaError_t launch_step(const Map& map, const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                               gsdf_track_stats* stats, const Scratch& sc, int num_sms, cudaStream_t st) {
+    const unsigned blocks = (unsigned)track_blocks(K, sc, num_sms);
+    track_kernel<Map, kTri><<<blocks, kTrackThreads, 0, st>>>(map, depth, K, prm, T_wc, stats, sc);
     return cudaGetLastError();
+}
+
+cudaError_t launch_track16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                           gsdf_track_stats* stats, const Scratch& sc, int num_sms, cudaStream_t st) {
+    return launch_step<HashMap16, false>(hm, depth, K, prm, T_wc, stats, sc, num_sms, st);
 }
 
 cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
                          const Params& prm, double* T_wc, gsdf_track_stats* stats,
                          const Scratch& sc, int num_sms, cudaStream_t st) {
-    const long long n_px = (long long)K.width * K.height;
-    long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
-    long long cap = (long long)kTrackBlocksPerSM * num_sms;
-    if (cap > sc.max_track_blocks) cap = sc.max_track_blocks;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    if (dm)
-        track_kernel<DenseMap><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*dm, depth, K, prm, T_wc, stats, sc);
-    else
-        track_kernel<HashMap><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*hm, depth, K, prm, T_wc, stats, sc);
-    return cudaGetLastError();
+    if (dm) return launch_step<DenseMap, false>(*dm, depth, K, prm, T_wc, stats, sc, num_sms, st);
+    return launch_step<HashMap, false>(*hm, depth, K, prm, T_wc, stats, sc, num_sms, st);
 }
 
 cudaError_t launch_track_trilinear(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
                                    const Params& prm, double* T_wc, gsdf_track_stats* stats, const Scratch& sc,
                                    int num_sms, cudaStream_t st) {
-    const long long n_px = (long long)K.width * K.height;
-    long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
-    long long cap = (long long)kTrackBlocksPerSM * num_sms;
-    if (cap > sc.max_track_blocks) cap = sc.max_track_blocks;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    if (dm)
-        track_kernel<DenseMap, true><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*dm, depth, K, prm, T_wc, stats, sc);
-    else
-        track_kernel<HashMap, true><<<(unsigned)blocks, kTrackThreads, 0, st>>>(*hm, depth, K, prm, T_wc, stats, sc);
-    return cudaGetLastError();
+    if (dm) return launch_step<DenseMap, true>(*dm, depth, K, prm, T_wc, stats, sc, num_sms, st);
+    return launch_step<HashMap, true>(*hm, depth, K, prm, T_wc, stats, sc, num_sms, st);
 }
 
 }  // namespace gsdf
@@ -184,6 +176,7 @@ extern "C" gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, con
     prm.inv_vs = (float)(1.0 / (double)voxel_size);
     prm.huber = huber_delta;
     prm.damping = damping;
+    prm.lam_scale = damping / 6.0;
     Scratch sc = {};
     sc.accum = scratch;
     sc.counter = (unsigned int*)(scratch + kAccumWords);
@@ -191,4 +184,46 @@ extern "C" gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, con
     const cudaError_t e = launch_track(&dm, nullptr, depth_dev, ki, prm, T_wc_dev, stats_dev, sc, sms, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GSDF_ERR_OOM : GSDF_ERR_CUDA;
     return GSDF_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Gauss-Newton update from given normal equations (the last stage of a tracking step on its
+// own): one warp per system, the same device solve and exponential map as the tracking kernels.
+// ------------------------------------------------------------------------------------------
+
+namespace gsdf {
+namespace {
+
+__global__ void __launch_bounds__(32) gn_update_kernel(const double* __restrict__ Hb,
+                                                       const int64_t* __restrict__ n_valid, double lam_scale,
+                                                       double* T, double* xi_out, int32_t* status) {
+    __shared__ double hb[32], xi[6], dT[12], Ts[16];
+    const size_t s = blockIdx.x;
+    const int lane = threadIdx.x;
+    hb[lane] = lane < 27 ? Hb[27 * s + lane] : 0.0;
+    if (lane < 16) Ts[lane] = T[16 * s + lane];
+    __syncwarp();
+    const double tr = hb[0] + hb[6] + hb[11] + hb[15] + hb[18] + hb[20];
+    const bool ok = solve6_warp(hb, tr, lam_scale, (long long)n_valid[s], xi);
+    if (ok) {
+        se3_exp_warp(xi, dT);
+        const double tn = compose_entry(dT, Ts);
+        if (lane < 12) T[16 * s + lane] = tn;
+    }
+    if (xi_out && lane < 6) xi_out[6 * s + lane] = ok ? xi[lane] : 0.0;
+    if (status && lane == 0) status[s] = ok ? (int32_t)GSDF_OK : (int32_t)GSDF_ERR_DEGENERATE;
+}
+
+}  // namespace
+}  // namespace gsdf
+
+extern "C" gsdf_status gsdf_gn_update(int32_t n, const double* Hb_dev, const int64_t* n_valid_dev, double damping,
+                                      double* T_dev, double* xi_dev, int32_t* status_dev, void* cuda_stream) {
+    using namespace gsdf;
+    if (n < 0 || !isfinite(damping) || damping < 0.0) return GSDF_ERR_INVALID_ARG;
+    if (n == 0) return GSDF_OK;
+    if (!Hb_dev || !n_valid_dev || !T_dev) return GSDF_ERR_INVALID_ARG;
+    gn_update_kernel<<<(unsigned)n, 32, 0, (cudaStream_t)cuda_stream>>>(Hb_dev, n_valid_dev, damping / 6.0, T_dev,
+                                                                        xi_dev, status_dev);
+    return cudaGetLastError() == cudaSuccess ? GSDF_OK : GSDF_ERR_CUDA;
 }

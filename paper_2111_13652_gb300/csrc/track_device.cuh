@@ -13,35 +13,134 @@ constexpr int kTrackWarps = kTrackThreads / 32;
 constexpr int kTerms = 30;
 static_assert(kAccumCopies == kTrackWarps, "the finishing block reads one accumulator copy per warp");
 
-// FP64 on this GPU: every FP64 warp instruction occupies the FP64 pipe for about 64 cycles,
-// whatever the number of active lanes, so FP64 code is costed in warp instructions on the
-// critical path.  The reduction and the solve keep the method's FP64 precision but use few of
-// them:
+// FP64 on this GPU: every FP64 warp instruction occupies the SM sub-partition's FP64 pipe for
+// about 64 cycles, whatever the number of active lanes, and two independent FP64 instructions of
+// one warp do not overlap; integer and FP32 instructions take a few cycles.  FP64 code is
+// therefore costed in FP64 warp instructions on the critical path, and the finishing code keeps
+// the method's FP64 arithmetic but issues few of them:
 //   * the grid-wide sum is exact fixed-point integer arithmetic (associative, hence deterministic
-//     in any order, and off the FP64 pipe);
+//     in any order) and is converted to FP64 with integer instructions, rounded once;
+//   * compares, maxima and power-of-two scalings of FP64 values act on their bit patterns;
 //   * the 6x6 system is solved by one warp holding one entry of the augmented upper triangle
-//     [H | -b] per lane (27 lanes), so that an elimination step is three FP64 instructions.
+//     [H | -b] per lane (27 lanes), two FP64 instructions per elimination step, and the
+//     exponential map evaluates its three coefficients and twelve entries side by side.
 
 // 2^k as a double (k within the normal exponent range)
 __device__ __forceinline__ double exp2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
 // e such that x * 2^-e lies in [0.5, 1), for finite x > 0 with a normal exponent
 __device__ __forceinline__ int exponent_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1022; }
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// -x by an integer xor of the sign bit (kept opaque, so that it is not turned into an FP64
+// negation; inside an fma operand write -x instead, which costs nothing)
+__device__ __forceinline__ double neg_d(double x) {
+    int hi = __double2hiint(x);
+    asm("xor.b32 %0, %0, 0x80000000;" : "+r"(hi));
+    return __hiloint2double(hi, __double2loint(x));
+}
+// x > 0 (false for zeros, negatives and NaN, true for +inf)
+__device__ __forceinline__ bool pos_d(double x) {
+    const long long b = dbits(x);
+    return b > 0 && b <= 0x7ff0000000000000ll;
+}
+// x * 2^k, exact, as an exponent update on the bit pattern; zeros are returned unchanged.  Sets
+// `slow` when x or the result is not a normal number (subnormal, overflow, inf, NaN), where the
+// returned value is meaningless and the caller must take another path.
+__device__ __forceinline__ double scale2(double x, int k, bool& slow) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int e = (hi >> 20) & 0x7ff;
+    const bool zero = ((hi & 0x7fffffff) | lo) == 0;
+    slow = !zero && ((unsigned)(e - 1) >= 2046u || (unsigned)(e + k - 1) >= 2046u);
+    return zero ? x : __hiloint2double(hi + (int)((unsigned)k << 20), lo);
+}
 
-// Solve (H + lambda I) xi = -b, lambda = damping * mean(diag H), with one warp.  Hb (shared):
-// the 21 upper-triangle terms of H (row-major) then the 6 of b.  Degenerate (returns false,
-// xi = 0; uniform across the warp) if fewer than 6 residuals, a non-positive diagonal entry, or
-// an LDL^T pivot d_j <= 1e-12 max diag (the test of the Cholesky factorisation).
+// lane of entry (i, k), i <= k <= 6, of the augmented upper triangle; index of (i, k), k < 6,
+// among the 21 upper-triangle terms of H
+__device__ __forceinline__ int aug_lane(int i, int k) { return i * 7 - i * (i - 1) / 2 + (k - i); }
+__device__ __forceinline__ int h21_index(int i, int k) { return i * 6 - i * (i - 1) / 2 + (k - i); }
+
+// The same solve by lane 0 alone: the damped matrix factorised in place by Cholesky (packed
+// lower triangle, row i at i (i + 1) / 2) with the pivot test s_j > 1e-12 max diag, then the two
+// triangular solves; every lane returns the outcome.  Taken only when the warp-parallel solve
+// below meets a value outside the normal FP64 range.
+static __device__ __noinline__ bool solve6_serial(const double* Hb, double tr, double lam_scale, long long n_valid,
+                                           double* xi) {
+    const int lane = threadIdx.x & 31;
+    int ok = 0;
+    if (lane == 0) {
+        double L[21], y[6];
+        const double lam = lam_scale != 0.0 ? lam_scale * tr : 0.0;
+        double maxd = 0.0;
+#pragma unroll 1
+        for (int i = 0; i < 6; ++i) {
+#pragma unroll 1
+            for (int k = 0; k < i; ++k) L[i * (i + 1) / 2 + k] = Hb[h21_index(k, i)];
+            const double dg = Hb[h21_index(i, i)] + lam;
+            L[i * (i + 1) / 2 + i] = dg;
+            maxd = dg > maxd ? dg : maxd;
+        }
+        ok = n_valid >= 6 && maxd > 0.0;
+#pragma unroll 1
+        for (int j = 0; j < 6 && ok; ++j) {
+            double* Lj = L + j * (j + 1) / 2;
+            double s = Lj[j];
+#pragma unroll 1
+            for (int k = 0; k < j; ++k) s -= Lj[k] * Lj[k];
+            ok = s > 1e-12 * maxd;
+            Lj[j] = sqrt(s);
+#pragma unroll 1
+            for (int i = j + 1; i < 6; ++i) {
+                double* Li = L + i * (i + 1) / 2;
+                double v = Li[j];
+#pragma unroll 1
+                for (int k = 0; k < j; ++k) v -= Li[k] * Lj[k];
+                Li[j] = v / Lj[j];
+            }
+        }
+        if (ok) {
+#pragma unroll 1
+            for (int i = 0; i < 6; ++i) {
+                double v = -Hb[21 + i];
+#pragma unroll 1
+                for (int k = 0; k < i; ++k) v -= L[i * (i + 1) / 2 + k] * y[k];
+                y[i] = v / L[i * (i + 1) / 2 + i];
+            }
+#pragma unroll 1
+            for (int i = 5; i >= 0; --i) {
+                double v = y[i];
+#pragma unroll 1
+                for (int k = i + 1; k < 6; ++k) v -= L[k * (k + 1) / 2 + i] * xi[k];
+                xi[i] = v / L[i * (i + 1) / 2 + i];
+            }
+        }
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Solve (H + lambda I) xi = -b, lambda = damping * trace(H) / 6 = lam_scale * tr, with one warp
+// (the damped Gauss-Newton step of Sec. 4.1).  Hb (shared): the 21 upper-triangle terms of H
+// (row-major) then the 6 of b; tr = trace(H) as the caller has it; lam_scale = damping / 6.
+// Degenerate (returns false, uniform across the warp) if fewer than 6 residuals, a diagonal
+// entry of H + lambda I that is not positive, or an LDL^T pivot d_j <= 1e-12 max diag (the test
+// of the Cholesky factorisation).  Otherwise writes xi (shared) and returns true.
 //
-// Method: the rows and columns are scaled by powers of two s_i ~ diag_i^-1/2 (exact), then
-// eliminated without division: step j replaces every row i > j by
-//     n_j (p_j row_i - a_ij row_j),   p_j = current pivot, n_j = 2^-e with p_j n_j in [1/2, 1),
-// which equals the Schur-complement row times p_j n_j.  Row j is therefore row j of the LDL^T
-// factor scaled by sigma_j = prod_{k<j} p_k n_k, so d_j (of the scaled matrix) = p_j / sigma_j
-// and the pivot test is p_j > thr_j sigma_j with thr_j = 1e-12 maxd s_j^2, evaluated after the
-// elimination.  Back-substitution uses the six pivot reciprocals, formed in parallel.
-__device__ __forceinline__ bool solve6_warp(const double* Hb, double damping, long long n_valid, double* xi) {
+// Method: rows and columns are scaled by powers of two s_i ~ diag_i^-1/2 (exact), then
+// Gauss-Jordan elimination without division: step j replaces every row i != j by
+//     n_j (p_j row_i - a_ij row_j),   p_j = current pivot, n_j = 2^-e with p_j n_j in [1/2, 1)
+// (for i > j, a_ij = a_ji by symmetry of the trailing block, which holds exactly since the
+// update is symmetric).  The rows below j are the Schur complement times sigma_{j+1} =
+// prod_{k<=j} p_k n_k, so d_j (of the scaled matrix) = p_j / sigma_j and the pivot test is
+// p_j > 1e-12 maxd s_j^2 sigma_j; lane 27, which holds no entry, forms c sigma_j (c = 1e-12
+// maxd) inside the steps' own multiply instruction.  At the end row i reads d_i x_i = c_i, and the
+// six quotients are formed at once from a hardware reciprocal estimate refined by Newton's
+// iteration (relative error of order the square of the estimate's), then one correction of the
+// quotient against its residual.  Powers of two are applied to the bit patterns; a value that
+// leaves the normal range on the way sends the system to solve6_serial.
+__device__ __forceinline__ bool solve6_warp(const double* Hb, double tr, double lam_scale, long long n_valid,
+                                            double* xi) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
+    constexpr int kTestLane = 27;
     // lane -> entry (i, k) of the augmented upper triangle, 0 <= i <= 5, i <= k <= 6 (k = 6: rhs)
     int ei = 0, ek = 0;
     {
@@ -57,142 +156,144 @@ __device__ __forceinline__ bool solve6_warp(const double* Hb, double damping, lo
         }
     }
     const bool active = lane < 27;
-    auto idx = [](int i, int k) { return i * 7 - i * (i - 1) / 2 + (k - i); };  // lane of entry (i, k), i <= k
-    auto h21 = [](int i, int k) { return i * 6 - i * (i - 1) / 2 + (k - i); };  // index in the 21 terms
+    const bool test_lane = lane == kTestLane;
 
-    // lane-parallel bookkeeping: lane j < 6 owns diagonal entry j
-    const int dj = lane < 6 ? lane : 0;
-    const double myd = lane < 6 ? Hb[h21(dj, dj)] : 0.0;
-    double tr = myd;
-    tr += __shfl_xor_sync(full, tr, 1);
-    tr += __shfl_xor_sync(full, tr, 2);
-    tr += __shfl_xor_sync(full, tr, 4);  // lanes 0..7 hold the trace (lanes 6, 7 contribute 0)
-    tr = __shfl_sync(full, tr, 0);
-    const double lam = damping > 0.0 ? damping * tr * (1.0 / 6.0) : 0.0;
-    const double mydl = myd + lam;
-    double mx = lane < 6 ? mydl : -1.0;
-    mx = fmax(mx, __shfl_xor_sync(full, mx, 1));
-    mx = fmax(mx, __shfl_xor_sync(full, mx, 2));
-    mx = fmax(mx, __shfl_xor_sync(full, mx, 4));
-    const double maxd = __shfl_sync(full, mx, 0);
-    const bool bad_diag = __any_sync(full, lane < 6 && !(mydl > 0.0));
-    if (lane < 6) xi[lane] = 0.0;
-    if (n_valid < 6 || !(maxd > 0.0) || bad_diag) return false;
-    // power-of-two scales s_j ~ diag_j^-1/2 (exact); lane j < 6 computes its own
-    const double my_s = exp2i(-(exponent_of(lane < 6 ? mydl : 1.0) >> 1));
-    const double s_i = __shfl_sync(full, my_s, ei);
-    // (every lane must execute each shuffle: take it unconditionally, select afterwards)
-    const double s_k_sh = __shfl_sync(full, my_s, ek < 6 ? ek : 0);
-    const double s_k = ek < 6 ? s_k_sh : 1.0;
-    double a = 0.0;
-    if (active) a = ek < 6 ? (Hb[h21(ei, ek < 6 ? ek : 0)] + (ei == ek ? lam : 0.0)) : -Hb[21 + ei];
-    a *= s_i * s_k;
+    // entries with the damping on the diagonal: one FP64 instruction for the warp
+    double h = 0.0;
+    if (active) h = ek < 6 ? Hb[h21_index(ei, ek)] : neg_d(Hb[21 + ei]);
+    const double hl = fma(lam_scale, tr, h);
+    double a = (active && ei == ek && (dbits(lam_scale) << 1) != 0) ? hl : h;
 
-    double pn_mine = 1.0;  // lane (j, j) keeps p_j n_j of its step
+    // lane j < 6: damped diagonal d_j; positivity, maximum (on the bit patterns), scale 2^k_j
+    const int dl = lane < 6 ? lane : 0;
+    const double dj = __shfl_sync(full, a, aug_lane(dl, dl));
+    const bool bad_diag = __any_sync(full, lane < 6 && !pos_d(dj));
+    if (n_valid < 6 || bad_diag) return false;
+    const long long djb = dbits(dj);
+    const unsigned mhi = __reduce_max_sync(full, lane < 6 ? (unsigned)(djb >> 32) : 0u);
+    const unsigned mlo = __reduce_max_sync(full, (lane < 6 && (unsigned)(djb >> 32) == mhi) ? (unsigned)djb : 0u);
+    const double maxd = __longlong_as_double((long long)(((unsigned long long)mhi << 32) | mlo));
+    const int my_k = -(exponent_of(lane < 6 ? dj : 1.0) >> 1);
+    const int k_i = __shfl_sync(full, my_k, ei);
+    const int k_k = __shfl_sync(full, my_k, ek < 6 ? ek : 0);
+    bool slow = false, sl;
+    a = scale2(a, k_i + (ek < 6 ? k_k : 0), sl);
+    slow |= active && sl;
+
+    double cs = maxd;       // test lane: c sigma_j once step j's multiply has run
+    double mul = 1e-12;     // test lane: its factor in step j's multiply (then p_{j-1} n_{j-1})
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        const int jj = idx(j, j);
-        const double p = __shfl_sync(full, a, jj);
-        const double nrm = exp2i(-exponent_of(p > 0.0 ? p : 1.0));
-        const double an = a * nrm;
-        const double pn = __shfl_sync(full, an, jj);
-        if (lane == jj) pn_mine = pn;
-        const int src_n = idx(j, ei > j ? ei : j);
-        const int src_k = idx(j, ek > j ? ek : j);
-        const double aji_n = __shfl_sync(full, an, src_n);
-        const double ajk = __shfl_sync(full, a, src_k);
-        const double upd = fma(-aji_n, ajk, pn * a);
-        if (active && ei > j) a = upd;
+        const double p = __shfl_sync(full, a, aug_lane(j, j));
+        const double m = __shfl_sync(full, a, ei > j ? aug_lane(j, ei) : aug_lane(ei < j ? ei : j, j));
+        const double ajk = __shfl_sync(full, a, aug_lane(j, ek > j ? ek : j));
+        const int kj = __shfl_sync(full, my_k, j);
+        const bool upd_row = active && ei != j && ek > j;   // rows i != j, columns right of j
+        const bool upd = upd_row || (active && ei == ek && ei < j);  // or the diagonal of an earlier pivot row
+        const double pa = (test_lane ? mul : p) * (test_lane ? cs : a);
+        const double t = fma(-m, upd_row ? ajk : 0.0, pa);
+        const bool ppos = pos_d(p);
+        const int ep = exponent_of(ppos ? p : 1.0);
+        const double ts = scale2(t, -ep, sl);
+        slow |= upd && sl;
+        a = upd ? ts : a;
+        // the pivot test of row j, meaningful on the test lane: p_j > c sigma_j s_j^2
+        const double thr = scale2(pa, 2 * kj, sl);
+        slow |= test_lane && sl;
+        bad |= test_lane && !(ppos && dbits(p) > dbits(thr));
+        cs = pa;
+        mul = scale2(p, -ep, sl);
+        slow |= test_lane && ppos && sl;
     }
-    // pivot test, lane-parallel: lane j < 6 checks p_j > 1e-12 maxd s_j^2 sigma_j with
-    // sigma_j = prod_{k<j} p_k n_k (exclusive prefix product by shuffles)
-    const double pj = __shfl_sync(full, a, idx(dj, dj));
-    const double pnj = __shfl_sync(full, pn_mine, idx(dj, dj));
-    double pre = lane < 6 ? pnj : 1.0;  // inclusive prefix product over lanes 0..5
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        const double up = __shfl_up_sync(full, pre, o);
-        if (lane >= o) pre *= up;
-    }
-    double sigma = __shfl_up_sync(full, pre, 1);
-    if (lane == 0) sigma = 1.0;
-    const bool pivot_bad = __any_sync(full, lane < 6 && !(pj > (1e-12 * maxd) * (my_s * my_s) * sigma));
-    if (pivot_bad) return false;
-    // back-substitution on the rhs lanes (i, 6): x_k = c_k / p_k, c_i -= a_ik x_k
-    const double rcp = 1.0 / (ei == ek ? a : 1.0);        // lanes (k, k): 1 / p_k, all at once
-    double c = a;                                            // meaningful in lanes (i, 6)
-#pragma unroll
-    for (int k = 5; k >= 0; --k) {
-        const double rk = __shfl_sync(full, rcp, idx(k, k));
-        const double ck = __shfl_sync(full, c, idx(k, 6));
-        const double xk = ck * rk;
-        const double aik = __shfl_sync(full, a, idx(ei < k ? ei : k, k));
-        if (ek == 6 && ei < k) c = fma(-aik, xk, c);
-        if (ek == 6 && ei == k) c = xk;
-    }
-    if (active && ek == 6) xi[ei] = c * s_i;
+    // lanes (i, 6): x_i = c_i / d_i, then unscaled by s_i
+    const double d = __shfl_sync(full, a, aug_lane(ei, ei));
+    double r0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(d));
+    const double r1 = fma(r0, fma(-d, r0, 1.0), r0);
+    const double q0 = a * r1;
+    const double x = scale2(fma(r1, fma(-d, q0, a), q0), k_i, sl);
+    slow |= active && ek == 6 && sl;
+    if (__any_sync(full, slow)) return solve6_serial(Hb, tr, lam_scale, n_valid, xi);
+    if (__any_sync(full, bad)) return false;
+    if (active && ek == 6) xi[ei] = x;
     __syncwarp();
     return true;
 }
 
-// exp of the twist xi = (omega, upsilon) by one warp: R = I + A [w]x + B [w]x^2,
-// t = (I + B [w]x + C [w]x^2) u, A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3,
-// [w]x^2 = w w^T - th^2 I.  For th^2 < 0.01 lanes 0..2 evaluate the coefficients' Taylor series
-// in th^2 (truncation error < 1e-21); larger angles use sincos.  Lanes 0..8 then write R and
-// lanes 9..11 t into dT (row-major 3x4, shared); xi is in shared memory.
+// exp of the twist xi = (omega, upsilon) by one warp (the update T <- exp(xi^) T of Sec. 4.1):
+// R = I + A [w]x + B [w]x^2, t = (I + B [w]x + C [w]x^2) u with A = sin(th)/th,
+// B = (1 - cos th)/th^2, C = (th - sin th)/th^3 and [w]x^2 = w w^T - th^2 I.  Lanes 0..8 write
+// R (entry (lane / 3, lane % 3)) and lanes 9..11 t into dT (row-major 3x4, shared); xi is in
+// shared memory.  For th^2 < 1e-2 lanes 12..14 evaluate the coefficients' Taylor series in th^2
+// up to th^8 (truncation error below th^10 / 11! < 3e-18), while the entry lanes form their
+// products in the same instructions: nine FP64 instructions in all.  Larger angles use sincos.
 __device__ __forceinline__ void se3_exp_warp(const double* xi, double* dT) {
     const int lane = threadIdx.x & 31;
-    const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    double coef;
-    if (th2 < 1e-2) {
-        // coefficient tables of sum_k (-1)^k x^k / (2k+1)!, /(2k+2)!, /(2k+3)!
-        constexpr double kA[8] = {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880, -1.0 / 39916800,
-                                  1.0 / 6227020800.0, -1.0 / 1307674368000.0};
-        constexpr double kB[8] = {1.0 / 2, -1.0 / 24, 1.0 / 720, -1.0 / 40320, 1.0 / 3628800, -1.0 / 479001600,
-                                  1.0 / 87178291200.0, -1.0 / 20922789888000.0};
-        constexpr double kC[8] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800,
-                                  -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0};
-        coef = lane == 0 ? kA[7] : (lane == 1 ? kB[7] : kC[7]);
-#pragma unroll
-        for (int k = 6; k >= 0; --k) coef = (lane == 0 ? kA[k] : (lane == 1 ? kB[k] : kC[k])) + th2 * coef;
+    const unsigned full = 0xffffffffu;
+    const double w0 = xi[0], w1 = xi[1], w2 = xi[2], u0 = xi[3], u1 = xi[4], u2 = xi[5];
+    const bool is_t = lane >= 9 && lane < 12;
+    const int r = lane < 9 ? lane / 3 : (is_t ? lane - 9 : 0);
+    const int c = lane < 9 ? lane - 3 * r : 0;
+    const int r1 = r == 2 ? 0 : r + 1, r2 = r == 0 ? 2 : r - 1;
+    auto pick = [](int k, double x0, double x1, double x2) { return k == 0 ? x0 : (k == 1 ? x1 : x2); };
+    const double wr = pick(r, w0, w1, w2), wc = pick(c, w0, w1, w2), ur = pick(r, u0, u1, u2);
+    // three-term dot products: (w x u)_r on the t lanes, w.u on lane 16, th^2 = w.w elsewhere
+    double a0 = w0, b0 = w0, a1 = w1, b1 = w1, a2 = w2, b2 = w2;
+    if (lane == 16) { b0 = u0; b1 = u1; b2 = u2; }
+    if (is_t) {
+        a0 = pick(r1, w0, w1, w2);
+        b0 = pick(r2, u0, u1, u2);
+        a1 = neg_d(pick(r2, w0, w1, w2));
+        b1 = pick(r1, u0, u1, u2);
+        a2 = 0.0;
+        b2 = 0.0;
+    }
+    const double dot = fma(a0, b0, fma(a1, b1, a2 * b2));
+    const double th2 = __shfl_sync(full, dot, 15);
+    const double wu = __shfl_sync(full, dot, 16);
+    // ([w]x^2)_rc = w_r w_c - [r == c] th2 on the R lanes, ([w]x^2 u)_r = w_r (w.u) - th2 u_r on
+    // the t lanes; coefficient lanes 12..14 hold A, B, C
+    double Y, coef;
+    if (dbits(th2) < dbits(1e-2)) {
+        constexpr double kA[5] = {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880};
+        constexpr double kB[5] = {1.0 / 2, -1.0 / 24, 1.0 / 720, -1.0 / 40320, 1.0 / 3628800};
+        constexpr double kC[5] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800};
+        auto kcoef = [&](int k) { return lane == 12 ? kA[k] : (lane == 13 ? kB[k] : kC[k]); };
+        const bool is_c = lane >= 12 && lane < 15;
+        // step 1: Horner's first step | R lanes: Y | t lanes: th2 u_r
+        const double s1 = fma(is_c ? kcoef(4) : (is_t ? ur : wr), is_c || is_t ? th2 : wc,
+                              is_c ? kcoef(3) : ((!is_t && r == c) ? neg_d(th2) : 0.0));
+        // step 2: Horner | t lanes: Y = w_r (w.u) - th2 u_r
+        const double s2 = fma(is_c ? s1 : wr, is_c ? th2 : wu, is_c ? kcoef(2) : neg_d(s1));
+        coef = fma(fma(s2, th2, kcoef(1)), th2, kcoef(0));
+        Y = is_t ? s2 : s1;
     } else {
         const double th = sqrt(th2);
         double sn, cs;
         sincos(th, &sn, &cs);
-        coef = lane == 0 ? sn / th : (lane == 1 ? (1.0 - cs) / th2 : (th - sn) / (th2 * th));
+        coef = lane == 12 ? sn / th : (lane == 13 ? (1.0 - cs) / th2 : (th - sn) / (th2 * th));
+        Y = is_t ? fma(wr, wu, -(th2 * ur)) : fma(wr, wc, r == c ? -th2 : 0.0);
     }
-    const double A = __shfl_sync(0xffffffffu, coef, 0);
-    const double B = __shfl_sync(0xffffffffu, coef, 1);
-    const double C = __shfl_sync(0xffffffffu, coef, 2);
-    // every lane evaluates one uniform expression  base + c1 X + c2 Y :
-    //   lanes 0..8  (R entry (r, c)):  I_rc + A [w]x_rc + B ([w]x^2)_rc
-    //   lanes 9..11 (t entry r):       u_r + B (w x u)_r + C (w_r (w.u) - th2 u_r)
-    const int r = lane < 9 ? lane / 3 : (lane < 12 ? lane - 9 : 0);
-    const int cc = lane < 9 ? lane - 3 * r : 0;
-    const bool is_t = lane >= 9;
-    const double u0 = xi[3], u1 = xi[4], u2 = xi[5];
-    const double wr = r == 0 ? w0 : (r == 1 ? w1 : w2);
-    const double wc = cc == 0 ? w0 : (cc == 1 ? w1 : w2);
-    const double ur = r == 0 ? u0 : (r == 1 ? u1 : u2);
-    // [w]x_rc for r != c: +-w_k with k the remaining index
-    const int kk = 3 - r - cc;
-    const double wk = kk == 0 ? w0 : (kk == 1 ? w1 : w2);
-    const double kx = (r == cc) ? 0.0 : (((cc - r + 3) % 3 == 1) ? -wk : wk);
-    // (w x u)_r = w_{r+1} u_{r+2} - w_{r+2} u_{r+1}
-    const int r1 = (r + 1) % 3, r2 = (r + 2) % 3;
-    const double wa = r1 == 0 ? w0 : (r1 == 1 ? w1 : w2), wb = r2 == 0 ? w0 : (r2 == 1 ? w1 : w2);
-    const double ua = r1 == 0 ? u0 : (r1 == 1 ? u1 : u2), ub = r2 == 0 ? u0 : (r2 == 1 ? u1 : u2);
-    const double wxu = fma(wa, ub, -(wb * ua));
-    const double wu = fma(w0, u0, fma(w1, u1, w2 * u2));
-    const double base = is_t ? ur : ((r == cc) ? 1.0 : 0.0);
-    const double c1 = is_t ? B : A;
-    const double c2 = is_t ? C : B;
-    const double X = is_t ? wxu : kx;
-    const double Y = is_t ? fma(wr, wu, -th2 * ur) : fma(wr, wc, (r == cc) ? -th2 : 0.0);
-    const double v = fma(c2, Y, fma(c1, X, base));
-    if (lane < 12) dT[is_t ? 4 * r + 3 : 4 * r + cc] = v;
+    const double A = __shfl_sync(full, coef, 12);
+    const double B = __shfl_sync(full, coef, 13);
+    const double C = __shfl_sync(full, coef, 14);
+    // [w]x_rc for r != c: -w_k if c follows r cyclically, +w_k otherwise (k the third index)
+    const double wk = pick(3 - r - c, w0, w1, w2);
+    const double X = is_t ? dot : (r == c ? 0.0 : (c == r1 ? neg_d(wk) : wk));
+    const double base = is_t ? ur : (r == c ? 1.0 : 0.0);
+    const double v = fma(is_t ? C : B, Y, fma(is_t ? B : A, X, base));
+    if (lane < 12) dT[is_t ? 4 * r + 3 : 4 * r + c] = v;
     __syncwarp();
+}
+
+// T <- dT T for the top three rows of a 4x4 rigid transform (row-major, shared), lanes 0..11
+// one entry each; returns the new entry (lane i*4+j) in the calling lanes.
+__device__ __forceinline__ double compose_entry(const double* dT, const double* T) {
+    const int lane = threadIdx.x & 31;
+    const int i = (lane >> 2) < 3 ? lane >> 2 : 0, j = lane & 3;
+    const double* d = dT + 4 * i;
+    return fma(d[2], T[8 + j], fma(d[1], T[4 + j], fma(d[0], T[j], j == 3 ? d[3] : 0.0)));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -201,25 +302,61 @@ __device__ __forceinline__ void se3_exp_warp(const double* xi, double* dT) {
 // added into 64-bit accumulator k.  Sums of up to 2^32 values are exact in any order.
 // ------------------------------------------------------------------------------------------
 
-__device__ __forceinline__ void fx_add(unsigned long long* acc4, double x) {
+// chunk q of a term lives at acc[q * stride]
+__device__ __forceinline__ void fx_add(unsigned long long* acc, int stride, double x) {
     const double fl = floor(x);
     const long long hi = (long long)fl;
     const unsigned long long lo = (unsigned long long)((x - fl) * 18446744073709551616.0);
     const unsigned long long uhi = (unsigned long long)hi;
-    atomicAdd(acc4 + 0, lo & 0xffffffffull);
-    atomicAdd(acc4 + 1, lo >> 32);
-    atomicAdd(acc4 + 2, uhi & 0xffffffffull);
-    atomicAdd(acc4 + 3, uhi >> 32);
+    atomicAdd(acc + 0 * stride, lo & 0xffffffffull);
+    atomicAdd(acc + 1 * stride, lo >> 32);
+    atomicAdd(acc + 2 * stride, uhi & 0xffffffffull);
+    atomicAdd(acc + 3 * stride, uhi >> 32);
 }
 
-// value of a fixed-point number given its four (possibly carry-laden) 64-bit chunk sums
-__device__ __forceinline__ double fx_value(unsigned long long c0, unsigned long long c1,
-                                          unsigned long long c2, unsigned long long c3) {
-    // v = c0 + c1 2^32 + c2 2^64 + c3 2^96 (mod 2^128)
-    const unsigned long long lo_a = c0 + (c1 << 32);
-    const unsigned long long carry = (lo_a < c0) ? 1ull : 0ull;
-    const unsigned long long hi = (c1 >> 32) + c2 + (c3 << 32) + carry;
-    return (double)(long long)hi + (double)lo_a * 5.421010862427522e-20;  // lo * 2^-64
+// the 128-bit value c0 + c1 2^32 + c2 2^64 + c3 2^96 (mod 2^128) of four chunk sums, as hi:lo
+__device__ __forceinline__ void fx_join(unsigned long long c0, unsigned long long c1, unsigned long long c2,
+                                        unsigned long long c3, unsigned long long& lo, unsigned long long& hi) {
+    lo = c0 + (c1 << 32);
+    hi = (c1 >> 32) + c2 + (c3 << 32) + (lo < c0 ? 1ull : 0ull);
+}
+
+// the two's-complement fixed-point number hi:lo * 2^-64 as the nearest double (ties to even),
+// with integer instructions only
+__device__ __forceinline__ double fx_to_double(unsigned long long lo, unsigned long long hi) {
+    const bool neg = (long long)hi < 0;
+    if (neg) {  // magnitude: ~v + 1
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    if ((hi | lo) == 0ull) return 0.0;
+    // top: the 64 leading bits of the magnitude (most significant bit set); rest: the bits below;
+    // the magnitude lies in [2^(n-1), 2^n)
+    int n;
+    unsigned long long top, rest;
+    if (hi != 0ull) {
+        const int lz = __clzll((long long)hi);
+        top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+        rest = lo << lz;
+        n = 128 - lz;
+    } else {
+        const int lz = __clzll((long long)lo);
+        top = lo << lz;
+        rest = 0ull;
+        n = 64 - lz;
+    }
+    unsigned long long mant = top >> 11;  // 53 bits
+    const bool half = (top >> 10) & 1ull;
+    const bool sticky = (top & 0x3ffull) != 0ull || rest != 0ull;
+    if (half && (sticky || (mant & 1ull))) ++mant;
+    if (mant >> 53) {
+        mant >>= 1;
+        ++n;
+    }
+    // value = mant 2^(n - 53 - 64): biased exponent n - 65 + 1023
+    const unsigned long long bits = ((unsigned long long)(n + 958) << 52) | (mant & 0x000fffffffffffffull) |
+                                    (neg ? 0x8000000000000000ull : 0ull);
+    return __longlong_as_double((long long)bits);
 }
 
 // Reduce-scatter of 32 per-lane values over a warp by butterfly exchange (31 shuffles instead of
@@ -249,7 +386,7 @@ struct TrackShared {
     float Rt[12];  // R (row-major) and t rounded once to FP32
     double Tsh[16];
     double part[kTrackWarps][32];
-    unsigned long long csum[kAccumCopies][32][4];
+    unsigned long long tsum[4][32];  // chunk sums of the 32 term slots (finishing block)
     double xi[6], dT[12];
     int flag;
 };
@@ -393,10 +530,12 @@ __device__ __forceinline__ void block_reduce_terms(TrackShared& sh, float (&acc)
 }
 
 // Add the block totals to accumulator copy `copy` of a scene and take a ticket; returns (in
-// every thread) whether this block was the scene's last of `n_parts`.
+// every thread) whether this block was the scene's last of `n_parts`.  Accumulator layout:
+// word (copy * 4 + chunk) * 32 + term, so that the four chunk additions of the 30 terms and the
+// finishing reads are contiguous.
 __device__ __forceinline__ bool add_partial_and_ticket(TrackShared& sh, unsigned long long* accum,
                                                        unsigned int* counter, int copy, unsigned n_parts) {
-    if (threadIdx.x < kTerms) fx_add(accum + ((copy % kAccumCopies) * 32 + threadIdx.x) * 4, sh.part[0][threadIdx.x]);
+    if (threadIdx.x < kTerms) fx_add(accum + (copy % kAccumCopies) * 128 + threadIdx.x, 32, sh.part[0][threadIdx.x]);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -413,40 +552,46 @@ __device__ __forceinline__ bool add_partial_and_ticket(TrackShared& sh, unsigned
 __device__ __forceinline__ void finish_scene(TrackShared& sh, unsigned long long* accum, unsigned int* counter,
                                              const Params& prm, double* T_wc, gsdf_track_stats* stats) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __threadfence();
-    {
-        unsigned long long* src = accum + ((size_t)warp * 32 + lane) * 4;
+    const unsigned full = 0xffffffffu;
+    if (warp < 4) {
+        // warp q sums chunk q of the 32 term slots over the copies (one coalesced load per copy)
+        // and clears them for the next step
+        __threadfence();
+        unsigned long long* col = accum + warp * 32 + lane;
+        unsigned long long s[kAccumCopies];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            sh.csum[warp][lane][q] = __ldcg(src + q);
-            src[q] = 0ull;
-        }
-    }
-    __syncthreads();
+        for (int c = 0; c < kAccumCopies; ++c) s[c] = __ldcg(col + c * 128);
 #pragma unroll
-    for (int h = kAccumCopies / 2; h > 0; h >>= 1) {
-        if (warp < h) {
+        for (int c = 0; c < kAccumCopies; ++c) col[c * 128] = 0ull;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sh.csum[warp][lane][q] += sh.csum[warp + h][lane][q];
-        }
-        __syncthreads();
+        for (int h = kAccumCopies / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int c = 0; c < h; ++c) s[c] += s[c + h];
+        // slot 30 (empty otherwise): the trace of H, as the sum of the diagonal terms' chunks
+        unsigned long long tr = 0ull;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tr += __shfl_sync(full, s[0], h21_index(i, i));
+        sh.tsum[warp][lane] = lane == 30 ? tr : s[0];
+        asm volatile("bar.sync 1, 128;" ::: "memory");
     }
     if (warp == 0) {
-        sh.part[0][lane] = lane < kTerms ? fx_value(sh.csum[0][lane][0], sh.csum[0][lane][1], sh.csum[0][lane][2],
-                                                    sh.csum[0][lane][3])
-                                         : 0.0;
+        // lanes 0..29 the terms, lane 30 the trace: exact sums rounded once to FP64
+        unsigned long long lo, hi;
+        fx_join(sh.tsum[0][lane], sh.tsum[1][lane], sh.tsum[2][lane], sh.tsum[3][lane], lo, hi);
+        const double v = fx_to_double(lo, hi);
+        sh.part[0][lane] = v;
+        // the counts are whole numbers: their integer part is exact
+        const long long n_valid = (long long)__shfl_sync(full, hi, 28);
+        const long long n_huber = (long long)__shfl_sync(full, hi, 29);
+        const double tr = __shfl_sync(full, v, 30);
         __syncwarp();
         const double* total = sh.part[0];
         if (lane == 0) *counter = 0u;
-        const long long n_valid = (long long)(total[28] + 0.5);
-        const bool ok = solve6_warp(total, prm.damping, n_valid, sh.xi);
-        if (ok) se3_exp_warp(sh.xi, sh.dT);
-        // T <- dT * T: lanes 0..11 compute one entry each of the top three rows
-        if (ok && lane < 12) {
-            const int i = lane >> 2, j = lane & 3;
-            double tn = (sh.dT[4 * i + 0] * sh.Tsh[j] + sh.dT[4 * i + 1] * sh.Tsh[4 + j]) + sh.dT[4 * i + 2] * sh.Tsh[8 + j];
-            if (j == 3) tn += sh.dT[4 * i + 3];
-            T_wc[lane] = tn;
+        const bool ok = solve6_warp(total, tr, prm.lam_scale, n_valid, sh.xi);
+        if (ok) {
+            se3_exp_warp(sh.xi, sh.dT);
+            const double tn = compose_entry(sh.dT, sh.Tsh);  // T <- dT T, lanes 0..11
+            if (lane < 12) T_wc[lane] = tn;
         }
         if (stats) {
             if (lane < 21) stats->H[lane] = total[lane];
@@ -455,7 +600,7 @@ __device__ __forceinline__ void finish_scene(TrackShared& sh, unsigned long long
             if (lane == 0) {
                 stats->energy = total[27];
                 stats->n_valid = n_valid;
-                stats->n_huber = (long long)(total[29] + 0.5);
+                stats->n_huber = n_huber;
                 stats->status = ok ? (int)GSDF_OK : (int)GSDF_ERR_DEGENERATE;
                 stats->pad = 0;
             }

@@ -107,6 +107,8 @@ _SIGS = {
     "gsdf_track_step_dense_noalloc": (C.c_int, [C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p,
                                                 _P(C.c_int32), _P(C.c_int32), C.c_float, C.c_float, C.c_double,
                                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gsdf_gn_update": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
     "gsdf_energy_create": (C.c_int, [C.c_int64, C.c_void_p, C.c_float, C.c_int32, _P(gsdf_intrinsics), C.c_void_p,
                                      C.c_void_p, C.c_void_p, _P(C.c_void_p)]),
     "gsdf_energy_destroy": (C.c_int, [C.c_void_p]),
@@ -236,6 +238,35 @@ def gsdf_track_step_dense_noalloc(depth_ptr: int, K: gsdf_intrinsics, A_ptr: int
     return load_library().gsdf_track_step_dense_noalloc(
         C.c_void_p(depth_ptr), C.byref(K), C.c_void_p(A_ptr), C.c_void_p(W_ptr), d, o, voxel_size, huber_delta,
         damping, C.c_void_p(pose_ptr), C.c_void_p(stats_ptr or None), C.c_void_p(stream or None))
+
+
+def gsdf_gn_update(n: int, Hb_ptr: int, n_valid_ptr: int, damping: float, T_ptr: int, xi_ptr: int = 0,
+                   status_ptr: int = 0, stream: int = 0) -> int:
+    v = lambda x: C.c_void_p(x or None)  # noqa: E731
+    return load_library().gsdf_gn_update(n, v(Hb_ptr), v(n_valid_ptr), damping, v(T_ptr), v(xi_ptr), v(status_ptr),
+                                         v(stream))
+
+
+def gn_update(Hb, n_valid, damping: float, T, xi=None, status=None, stream=None):
+    """Damped Gauss-Newton updates T <- exp(xi^) T of n poses from given normal equations
+    (gsdf_gn_update): Hb (n, 27) float64 (21 upper-triangle terms of H, then b), n_valid (n,)
+    int64, T (n, 4, 4) float64 updated in place, optional outputs xi (n, 6) float64 and status
+    (n,) int32; all contiguous CUDA tensors."""
+    import torch
+
+    n = int(Hb.shape[0])
+    want = [("Hb", Hb, torch.float64, (n, 27)), ("n_valid", n_valid, torch.int64, (n,)),
+            ("T", T, torch.float64, (n, 4, 4))]
+    if xi is not None:
+        want.append(("xi", xi, torch.float64, (n, 6)))
+    if status is not None:
+        want.append(("status", status, torch.int32, (n,)))
+    for name, x, dt, shape in want:
+        if not (x.is_cuda and x.dtype == dt and x.is_contiguous() and tuple(x.shape) == shape):
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of shape {shape}")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(gsdf_gn_update(n, Hb.data_ptr(), n_valid.data_ptr(), damping, T.data_ptr(), _ptr(xi), _ptr(status),
+                          s.cuda_stream), "gsdf_gn_update")
 
 
 def gsdf_status_string(s: int) -> str:

@@ -65,6 +65,12 @@ def test_argument_errors_without_gpu(lib_path):
     assert L.gsdf_destroy(None) == G.GSDF_ERR_INVALID_ARG
     assert L.gsdf_track_step(None, None, None, None, None) == G.GSDF_ERR_INVALID_ARG
     assert L.gsdf_integrate(None, None, None, None, None) == G.GSDF_ERR_INVALID_ARG
+    nul = [None] * 3
+    assert L.gsdf_gn_update(-1, None, None, 0.0, *nul, None) == G.GSDF_ERR_INVALID_ARG
+    assert L.gsdf_gn_update(0, None, None, 0.0, *nul, None) == G.GSDF_OK  # nothing to do
+    assert L.gsdf_gn_update(1, None, None, 0.0, *nul, None) == G.GSDF_ERR_INVALID_ARG
+    assert L.gsdf_gn_update(0, None, None, -1e-4, *nul, None) == G.GSDF_ERR_INVALID_ARG
+    assert L.gsdf_gn_update(0, None, None, float("nan"), *nul, None) == G.GSDF_ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header(tmp_path):
