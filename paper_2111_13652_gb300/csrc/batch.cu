@@ -91,8 +91,8 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
             for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
                 track_pixel(m, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
         }
-        block_reduce_terms(sh, acc);
-        if (add_partial_and_ticket(sh, d->accum, d->ticket, lt, (unsigned)d->n_tiles))
+        const unsigned long long s = block_reduce_terms(sh, acc);
+        if (add_partial_and_ticket(sh, s, d->accum, d->ticket, lt, (unsigned)d->n_tiles))
             finish_scene(sh, d->accum, d->ticket, prm, d->pose, d->tstats);
         __syncthreads();
     }

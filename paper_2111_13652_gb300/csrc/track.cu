@@ -31,9 +31,9 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
         else
             track_pixel(map, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
     }
-    block_reduce_terms(sh, acc);
+    const unsigned long long s = block_reduce_terms(sh, acc);
     // block b adds into accumulator copy b mod kAccumCopies (spreads same-address atomics)
-    if (!add_partial_and_ticket(sh, sc.accum, sc.counter, blockIdx.x, gridDim.x)) return;
+    if (!add_partial_and_ticket(sh, s, sc.accum, sc.counter, blockIdx.x, gridDim.x)) return;
     finish_scene(sh, sc.accum, sc.counter, prm, T_wc, stats);
 }
 

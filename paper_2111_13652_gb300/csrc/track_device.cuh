@@ -297,21 +297,42 @@ __device__ __forceinline__ double compose_entry(const double* dT, const double* 
 }
 
 // ------------------------------------------------------------------------------------------
-// exact fixed-point accumulation: a double x (|x| < 2^62) is rounded toward -inf to a multiple of
+// exact fixed-point accumulation: a value x (|x| < 2^62) is rounded toward -inf to a multiple of
 // 2^-64 and held as a 128-bit two's-complement integer, split into four 32-bit chunks; chunk k is
 // added into 64-bit accumulator k.  Sums of up to 2^32 values are exact in any order.
 // ------------------------------------------------------------------------------------------
 
-// chunk q of a term lives at acc[q * stride]
-__device__ __forceinline__ void fx_add(unsigned long long* acc, int stride, double x) {
-    const double fl = floor(x);
-    const long long hi = (long long)fl;
-    const unsigned long long lo = (unsigned long long)((x - fl) * 18446744073709551616.0);
-    const unsigned long long uhi = (unsigned long long)hi;
-    atomicAdd(acc + 0 * stride, lo & 0xffffffffull);
-    atomicAdd(acc + 1 * stride, lo >> 32);
-    atomicAdd(acc + 2 * stride, uhi & 0xffffffffull);
-    atomicAdd(acc + 3 * stride, uhi >> 32);
+// the four chunks of the fixed-point form of a float, with integer instructions only
+__device__ __forceinline__ void fx_chunks(float v, unsigned (&c)[4]) {
+    const unsigned b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);
+    const unsigned m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    // |v| 2^64 = m 2^p
+    const int p = (e ? e : 1) - 150 + 64;
+    unsigned long long lo = 0ull, hi = 0ull;
+    bool inexact = false;
+    if (p >= 64) {
+        hi = p < 128 ? (unsigned long long)m << (p - 64) : 0ull;
+    } else if (p >= 0) {
+        lo = (unsigned long long)m << p;
+        hi = p > 40 ? (unsigned long long)m >> (64 - p) : 0ull;
+    } else {
+        const int s = -p;
+        lo = s < 32 ? (unsigned long long)(m >> s) : 0ull;
+        inexact = s < 32 ? (m & ((1u << s) - 1u)) != 0u : m != 0u;
+    }
+    if (b >> 31) {  // floor(-|v| 2^64) = ~M + 1 - inexact
+        lo = ~lo;
+        hi = ~hi;
+        if (!inexact) {
+            ++lo;
+            if (lo == 0ull) ++hi;
+        }
+    }
+    c[0] = (unsigned)lo;
+    c[1] = (unsigned)(lo >> 32);
+    c[2] = (unsigned)hi;
+    c[3] = (unsigned)(hi >> 32);
 }
 
 // the 128-bit value c0 + c1 2^32 + c2 2^64 + c3 2^96 (mod 2^128) of four chunk sums, as hi:lo
@@ -385,7 +406,8 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
 struct TrackShared {
     float Rt[12];  // R (row-major) and t rounded once to FP32
     double Tsh[16];
-    double part[kTrackWarps][32];
+    unsigned wchunk[kTrackWarps][4][32];  // per-warp fixed-point chunks of the 32 term slots
+    double total[32];                     // finishing block: the scene's sums in FP64
     unsigned long long tsum[4][32];  // chunk sums of the 32 term slots (finishing block)
     double xi[6], dT[12];
     int flag;
@@ -516,31 +538,40 @@ __device__ __forceinline__ void track_pixel_trilinear(const Map& map, const floa
     acc[29] += ar > delta ? 1.0f : 0.0f;
 }
 
-// Block reduction of the per-thread terms: warps reduce-scatter (lane l <- term l), then a fixed
-// FP64 tree over the warps leaves the block totals in part[0][0..29].  All threads call it.
-__device__ __forceinline__ void block_reduce_terms(TrackShared& sh, float (&acc)[32]) {
+// Block reduction of the per-thread terms into exact fixed-point sums: every warp reduce-
+// scatters its terms in FP32 (lane l <- term l) and converts each warp sum to its four
+// fixed-point chunks with integer instructions; warp q < 4 then sums chunk q of the 32 term
+// slots over the warps.  Returns, in threads 0..127, chunk threadIdx.x / 32 of the block sum of
+// term threadIdx.x % 32 (0 elsewhere).  All threads call it.
+__device__ __forceinline__ unsigned long long block_reduce_terms(TrackShared& sh, float (&acc)[32]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    sh.part[warp][lane] = (double)warp_reduce_scatter32(acc);
-    __syncthreads();
+    unsigned c[4];
+    fx_chunks(warp_reduce_scatter32(acc), c);
 #pragma unroll
-    for (int h = kTrackWarps / 2; h > 0; h >>= 1) {
-        if (warp < h) sh.part[warp][lane] += sh.part[warp + h][lane];
-        __syncthreads();
+    for (int q = 0; q < 4; ++q) sh.wchunk[warp][q][lane] = c[q];
+    __syncthreads();
+    unsigned long long s = 0ull;
+    if (warp < 4) {
+#pragma unroll
+        for (int w = 0; w < kTrackWarps; ++w) s += sh.wchunk[w][warp][lane];
     }
+    return s;
 }
 
-// Add the block totals to accumulator copy `copy` of a scene and take a ticket; returns (in
-// every thread) whether this block was the scene's last of `n_parts`.  Accumulator layout:
-// word (copy * 4 + chunk) * 32 + term, so that the four chunk additions of the 30 terms and the
-// finishing reads are contiguous.
-__device__ __forceinline__ bool add_partial_and_ticket(TrackShared& sh, unsigned long long* accum,
-                                                       unsigned int* counter, int copy, unsigned n_parts) {
-    if (threadIdx.x < kTerms) fx_add(accum + (copy % kAccumCopies) * 128 + threadIdx.x, 32, sh.part[0][threadIdx.x]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(counter, 1u);
-        sh.flag = (ticket == n_parts - 1) ? 1 : 0;
+// Add a block's chunk sums (from block_reduce_terms) to accumulator copy `copy` of a scene and
+// take a ticket; returns (in every thread) whether this block was the scene's last of
+// `n_parts`.  Accumulator layout: word (copy * 4 + chunk) * 32 + term, so that the additions
+// and the finishing reads are contiguous.  Only warps 0..3 write, so only they fence before the
+// ticket.
+__device__ __forceinline__ bool add_partial_and_ticket(TrackShared& sh, unsigned long long s,
+                                                       unsigned long long* accum, unsigned int* counter, int copy,
+                                                       unsigned n_parts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < 4) {
+        if (lane < kTerms) atomicAdd(accum + (copy % kAccumCopies) * 128 + warp * 32 + lane, s);
+        __threadfence();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (threadIdx.x == 0) sh.flag = (atomicAdd(counter, 1u) == n_parts - 1) ? 1 : 0;
     }
     __syncthreads();
     return sh.flag != 0;
@@ -579,13 +610,13 @@ __device__ __forceinline__ void finish_scene(TrackShared& sh, unsigned long long
         unsigned long long lo, hi;
         fx_join(sh.tsum[0][lane], sh.tsum[1][lane], sh.tsum[2][lane], sh.tsum[3][lane], lo, hi);
         const double v = fx_to_double(lo, hi);
-        sh.part[0][lane] = v;
+        sh.total[lane] = v;
         // the counts are whole numbers: their integer part is exact
         const long long n_valid = (long long)__shfl_sync(full, hi, 28);
         const long long n_huber = (long long)__shfl_sync(full, hi, 29);
         const double tr = __shfl_sync(full, v, 30);
         __syncwarp();
-        const double* total = sh.part[0];
+        const double* total = sh.total;
         if (lane == 0) *counter = 0u;
         const bool ok = solve6_warp(total, tr, prm.lam_scale, n_valid, sh.xi);
         if (ok) {
