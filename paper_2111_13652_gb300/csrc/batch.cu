@@ -82,14 +82,16 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
         float acc[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+        const int pix0 = p0 + threadIdx.x;
+        const float d0 = pix0 < p1 ? __ldg(depth + pix0) : 0.0f;
         if (d->kind == GSDF_GRID_DENSE) {
             const DenseMap m = d->dm;
-            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
-                track_pixel(m, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+            for_pixels(depth, pix0, p1, blockDim.x, d0,
+                       [&](float D, int pix) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc); });
         } else {
             const HashMap m = d->hm;
-            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
-                track_pixel(m, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+            for_pixels(depth, pix0, p1, blockDim.x, d0,
+                       [&](float D, int pix) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc); });
         }
         const unsigned long long s = block_reduce_terms(sh, acc);
         if (add_partial_and_ticket(sh, s, d->accum, d->ticket, lt, (unsigned)d->n_tiles))

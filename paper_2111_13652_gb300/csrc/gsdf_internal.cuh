@@ -100,8 +100,8 @@ struct DenseMap {
     // psi and the (unnormalised) gradient of voxel idx; false if unobserved (W = 0)
     __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
         const float w = __ldg(W + idx);
+        const float4 a = __ldg(A + idx);  // issued with W: both loads in flight at once
         if (!(w > 0.0f)) return false;
-        const float4 a = __ldg(A + idx);
         psi = __fdividef(a.x, w);
         gx = a.y;
         gy = a.z;
@@ -167,8 +167,8 @@ struct HashMap {
     }
     __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
         const float w = __ldg(W + idx);
+        const float4 a = __ldg(A + idx);  // issued with W: both loads in flight at once
         if (!(w > 0.0f)) return false;
-        const float4 a = __ldg(A + idx);
         psi = __fdividef(a.x, w);
         gx = a.y;
         gy = a.z;
@@ -198,9 +198,10 @@ struct HashMap16 {
     __device__ __forceinline__ long long find(int mx, int my, int mz) const { return base.find(mx, my, mz); }
     __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {
         const float w = __ldg(W + idx);
+        const ushort4 h = __ldg(H + idx);  // issued with W and the block scale
+        const float sb = __ldg(scale + (idx >> 9));
         if (!(w > 0.0f)) return false;
-        const ushort4 h = __ldg(H + idx);
-        psi = __half2float(__ushort_as_half(h.x)) * __ldg(scale + (idx >> 9));
+        psi = __half2float(__ushort_as_half(h.x)) * sb;
         gx = __half2float(__ushort_as_half(h.y));
         gy = __half2float(__ushort_as_half(h.z));
         gz = __half2float(__ushort_as_half(h.w));

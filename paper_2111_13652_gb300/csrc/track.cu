@@ -19,18 +19,20 @@ __global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
 track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, double* T_wc,
              gsdf_track_stats* stats, Scratch sc) {
     __shared__ TrackShared sh;
+    const int n_px = K.width * K.height;
+    const int pix0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const float d0 = pix0 < n_px ? __ldg(depth + pix0) : 0.0f;  // in flight with the pose load
     load_pose(sh, T_wc);
     __syncthreads();
     float acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
-    const int n_px = K.width * K.height;
-    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x) {
+    for_pixels(depth, pix0, n_px, gridDim.x * blockDim.x, d0, [&](float D, int pix) {
         if (kTrilinear)
-            track_pixel_trilinear(map, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+            track_pixel_trilinear(map, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
         else
-            track_pixel(map, depth, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
-    }
+            track_pixel(map, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+    });
     const unsigned long long s = block_reduce_terms(sh, acc);
     // block b adds into accumulator copy b mod kAccumCopies (spreads same-address atomics)
     if (!add_partial_and_ticket(sh, s, sc.accum, sc.counter, blockIdx.x, gridDim.x)) return;

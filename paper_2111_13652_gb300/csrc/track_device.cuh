@@ -426,13 +426,25 @@ __device__ __forceinline__ void load_pose(TrackShared& sh, const double* T_wc) {
     }
 }
 
+// Pixels pix0, pix0 + stride, ... < n_px of a depth image, each handed with its depth value to
+// f(D, pix); the next pixel's depth is loaded one iteration ahead, so that its latency overlaps
+// the current pixel's lookups.  d0 = depth[pix0] (loaded earlier by the caller if pix0 < n_px).
+template <class F>
+__device__ __forceinline__ void for_pixels(const float* __restrict__ depth, int pix0, int n_px, int stride, float d0,
+                                           F&& f) {
+    float Dn = d0;
+    for (int pix = pix0; pix < n_px; pix += stride) {
+        const float D = Dn;
+        if (pix + stride < n_px) Dn = __ldg(depth + pix + stride);
+        f(D, pix);
+    }
+}
+
 // Residual and Jacobian of one pixel (Eq. (taylor)), Huber-weighted, added to the 30 terms:
 // 21 of H = sum w J J^T, 6 of b = sum w J r, E = sum w r^2, n_valid, n_huber.
 template <class Map>
-__device__ __forceinline__ void track_pixel(const Map& map, const float* __restrict__ depth, const Intr& K,
-                                            const float* R, const float* t, const Params& prm, int pix,
-                                            float (&acc)[32]) {
-    const float D = __ldg(depth + pix);
+__device__ __forceinline__ void track_pixel(const Map& map, float D, const Intr& K, const float* R, const float* t,
+                                            const Params& prm, int pix, float (&acc)[32]) {
     if (!depth_ok(D, K.depth_max)) return;
     const int v = pix / K.width;
     const int u = pix - v * K.width;
@@ -480,10 +492,9 @@ __device__ __forceinline__ void track_pixel(const Map& map, const float* __restr
 // is floor(P (1/v_s)) on the FP32 index path; a = (P - v_s b) / v_s with v_s b split exactly.
 // Same Huber weighting and terms as track_pixel.
 template <class Map>
-__device__ __forceinline__ void track_pixel_trilinear(const Map& map, const float* __restrict__ depth,
-                                                      const Intr& K, const float* R, const float* t,
-                                                      const Params& prm, int pix, float (&acc)[32]) {
-    const float D = __ldg(depth + pix);
+__device__ __forceinline__ void track_pixel_trilinear(const Map& map, float D, const Intr& K, const float* R,
+                                                      const float* t, const Params& prm, int pix,
+                                                      float (&acc)[32]) {
     if (!depth_ok(D, K.depth_max)) return;
     const int v = pix / K.width;
     const int u = pix - v * K.width;
