@@ -86,12 +86,12 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
         const float d0 = pix0 < p1 ? __ldg(depth + pix0) : 0.0f;
         if (d->kind == GSDF_GRID_DENSE) {
             const DenseMap m = d->dm;
-            for_pixels(depth, pix0, p1, blockDim.x, d0,
-                       [&](float D, int pix) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc); });
+            for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
+                       [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
         } else {
             const HashMap m = d->hm;
-            for_pixels(depth, pix0, p1, blockDim.x, d0,
-                       [&](float D, int pix) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc); });
+            for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
+                       [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
         }
         const unsigned long long s = block_reduce_terms(sh, acc);
         if (add_partial_and_ticket(sh, s, d->accum, d->ticket, lt, (unsigned)d->n_tiles))

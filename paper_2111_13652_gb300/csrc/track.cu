@@ -27,11 +27,11 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
     float acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
-    for_pixels(depth, pix0, n_px, gridDim.x * blockDim.x, d0, [&](float D, int pix) {
+    for_pixels(depth, K.width, pix0, n_px, gridDim.x * blockDim.x, d0, [&](float D, int, int u, int v) {
         if (kTrilinear)
-            track_pixel_trilinear(map, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+            track_pixel_trilinear(map, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc);
         else
-            track_pixel(map, D, K, sh.Rt, sh.Rt + 9, prm, pix, acc);
+            track_pixel(map, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc);
     });
     const unsigned long long s = block_reduce_terms(sh, acc);
     // block b adds into accumulator copy b mod kAccumCopies (spreads same-address atomics)

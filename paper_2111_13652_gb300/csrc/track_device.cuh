@@ -426,17 +426,27 @@ __device__ __forceinline__ void load_pose(TrackShared& sh, const double* T_wc) {
     }
 }
 
-// Pixels pix0, pix0 + stride, ... < n_px of a depth image, each handed with its depth value to
-// f(D, pix); the next pixel's depth is loaded one iteration ahead, so that its latency overlaps
-// the current pixel's lookups.  d0 = depth[pix0] (loaded earlier by the caller if pix0 < n_px).
+// Pixels pix0, pix0 + stride, ... < n_px of a depth image of the given width, each handed with its
+// depth value and column/row to f(D, pix, u, v); the next pixel's depth is loaded one iteration
+// ahead, so that its latency overlaps the current pixel's lookups, and (u, v) advance by the
+// stride's own (column, row) offset instead of a division per pixel.  d0 = depth[pix0] (loaded
+// earlier by the caller if pix0 < n_px).
 template <class F>
-__device__ __forceinline__ void for_pixels(const float* __restrict__ depth, int pix0, int n_px, int stride, float d0,
-                                           F&& f) {
+__device__ __forceinline__ void for_pixels(const float* __restrict__ depth, int width, int pix0, int n_px,
+                                           int stride, float d0, F&& f) {
+    int v = pix0 / width, u = pix0 - v * width;
+    const int sv = stride / width, su = stride - sv * width;
     float Dn = d0;
     for (int pix = pix0; pix < n_px; pix += stride) {
         const float D = Dn;
         if (pix + stride < n_px) Dn = __ldg(depth + pix + stride);
-        f(D, pix);
+        f(D, pix, u, v);
+        u += su;
+        v += sv;
+        if (u >= width) {
+            u -= width;
+            ++v;
+        }
     }
 }
 
@@ -444,10 +454,8 @@ __device__ __forceinline__ void for_pixels(const float* __restrict__ depth, int 
 // 21 of H = sum w J J^T, 6 of b = sum w J r, E = sum w r^2, n_valid, n_huber.
 template <class Map>
 __device__ __forceinline__ void track_pixel(const Map& map, float D, const Intr& K, const float* R, const float* t,
-                                            const Params& prm, int pix, float (&acc)[32]) {
+                                            const Params& prm, int u, int v, float (&acc)[32]) {
     if (!depth_ok(D, K.depth_max)) return;
-    const int v = pix / K.width;
-    const int u = pix - v * K.width;
     float dw[3], P[3];
     ray_world(K, R, u, v, dw);
 #pragma unroll
@@ -493,11 +501,9 @@ __device__ __forceinline__ void track_pixel(const Map& map, float D, const Intr&
 // Same Huber weighting and terms as track_pixel.
 template <class Map>
 __device__ __forceinline__ void track_pixel_trilinear(const Map& map, float D, const Intr& K, const float* R,
-                                                      const float* t, const Params& prm, int pix,
+                                                      const float* t, const Params& prm, int u, int v,
                                                       float (&acc)[32]) {
     if (!depth_ok(D, K.depth_max)) return;
-    const int v = pix / K.width;
-    const int u = pix - v * K.width;
     float dw[3], P[3];
     ray_world(K, R, u, v, dw);
 #pragma unroll
