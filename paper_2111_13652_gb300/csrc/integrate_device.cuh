@@ -53,26 +53,49 @@ __device__ __forceinline__ bool pixel_normal(const float* __restrict__ depth, co
     return c >= prm.cos_max;
 }
 
-// Per-ray cache of the last block looked up: consecutive voxels of a ray mostly share a block.
+// Per-ray cache of the last block looked up (consecutive voxels of a ray mostly share a block),
+// and of one block found ahead: the block of the ray's last sample.  The first lookups of a warp's
+// rays happen at about the same step and run together; finding the far block in the same pass
+// spares each ray a second lookup later, which the lanes would reach at different steps.
 struct BlockCache {
     int bx = 0x7fffffff, by = 0, bz = 0;
     long long base = -1;  // payload index of local voxel 0, or -1 when the block is unusable
+    int fx = 0x7fffffff, fy = 0, fz = 0;
+    long long fbase = -1;  // the far block's payload index, -1 if unknown
+    bool ahead = false;    // the far block has been looked for
 };
 
 template <class Map>
 __device__ __forceinline__ long long voxel_index(const Map& map, int mx, int my, int mz, BlockCache& bc,
-                                                 int* err, unsigned int* n_new);
+                                                 int* err, unsigned int* n_new, const int* far);
 
+// The far block is only found, never inserted: a block is created by a weighted update to one of
+// its voxels (allocation stays exactly the set of updated blocks).  Not yet allocated, it is
+// looked up (and inserted) when the ray reaches it, as any block.
 template <>
 __device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, int mx, int my, int mz, BlockCache& bc,
-                                                          int* err, unsigned int* n_new) {
+                                                          int* err, unsigned int* n_new, const int* far) {
     const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
     if (bx != bc.bx || by != bc.by || bz != bc.bz) {
-        const long long idx = map.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
+        if (bc.fbase >= 0 && bx == bc.fx && by == bc.fy && bz == bc.fz) {
+            bc.base = bc.fbase;
+            bc.fbase = -1;
+        } else {
+            bc.base = map.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
+            if (!bc.ahead) {
+                bc.ahead = true;
+                const int fx = floor_div8(far[0]), fy = floor_div8(far[1]), fz = floor_div8(far[2]);
+                if (fx != bx || fy != by || fz != bz) {
+                    bc.fbase = map.find(fx * 8, fy * 8, fz * 8);
+                    bc.fx = fx;
+                    bc.fy = fy;
+                    bc.fz = fz;
+                }
+            }
+        }
         bc.bx = bx;
         bc.by = by;
         bc.bz = bz;
-        bc.base = idx;
     }
     if (bc.base < 0) return -1;
     return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
@@ -81,7 +104,8 @@ __device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, in
 // FP16 maps: the index returned addresses the frame's accumulators (entry * 512 + local)
 template <>
 __device__ __forceinline__ long long voxel_index<HashMap16>(const HashMap16& map, int mx, int my, int mz,
-                                                            BlockCache& bc, int* err, unsigned int* n_new) {
+                                                            BlockCache& bc, int* err, unsigned int* n_new,
+                                                            const int*) {
     const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
     if (bx != bc.bx || by != bc.by || bz != bc.bz) {
         const long long idx = map.base.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
@@ -114,7 +138,7 @@ __device__ __forceinline__ void scatter(const HashMap16& m, long long i, float4 
 
 template <>
 __device__ __forceinline__ long long voxel_index<DenseMap>(const DenseMap& map, int mx, int my, int mz, BlockCache&,
-                                                           int*, unsigned int*) {
+                                                           int*, unsigned int*, const int*) {
     return map.find(mx, my, mz);
 }
 
@@ -139,6 +163,15 @@ __device__ __forceinline__ void integrate_ray(const Map& map, const float* __res
     float dw[3];
     ray_world(K, pose.R, u, v, dw);
     const int Kb = prm.band_half;
+    const float inv_band = 1.0f / (prm.trunc - prm.eps);
+    // voxel of the ray's last sample (for the block found ahead)
+    int far[3];
+    {
+        const float z = __fadd_rn(D, __fmul_rn((float)Kb, prm.half_vs));
+        far[0] = round_voxel(ray_coord(z, dw[0], pose.t[0]), prm.inv_vs);
+        far[1] = round_voxel(ray_coord(z, dw[1], pose.t[1]), prm.inv_vs);
+        far[2] = round_voxel(ray_coord(z, dw[2], pose.t[2]), prm.inv_vs);
+    }
     int k = 0;
     int pmx = 0x7fffffff, pmy = 0, pmz = 0;
     BlockCache bc;
@@ -168,9 +201,9 @@ __device__ __forceinline__ void integrate_ray(const Map& map, const float* __res
         const float zv = __fadd_rn(dot_row(pose.RT + 6, vc), pose.tinv[2]);
         const float d = __fsub_rn(zv, D);
         if (d > prm.trunc || d < -prm.trunc) continue;
-        const float w = d <= prm.eps ? 1.0f : (prm.trunc - d) / (prm.trunc - prm.eps);
+        const float w = d <= prm.eps ? 1.0f : (prm.trunc - d) * inv_band;
         if (!(w > 0.0f)) continue;
-        const long long idx = voxel_index(map, mx, my, mz, bc, err, n_new);
+        const long long idx = voxel_index(map, mx, my, mz, bc, err, n_new, far);
         if (idx < 0) continue;
         scatter(map, idx, make_float4(w * d, w * nwx, w * nwy, w * nwz), w);
         ++visits;
