@@ -39,7 +39,7 @@ SEED = 2
 VOXEL = 0.01
 HASH_SLOTS = 1 << 18
 FALLBACK_HBM_GBS = 6800.0
-# algorithmic bytes per unit (see DESIGN.md): tracking reads 4 B of depth per pixel and, for each
+# algorithmic bytes per unit: tracking reads 4 B of depth per pixel and, for each
 # pixel with a usable voxel, one 8 B key probe and the 20 B payload; fusion reads 4 B of depth per
 # pixel and each ray-voxel update probes an 8 B key and read-modify-writes the 20 B payload.
 TRACK_B_PER_PX = 4
