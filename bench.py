@@ -60,6 +60,24 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x, world, device):
+    """The largest of a value over the ranks, on every rank (the slowest rank's time bounds the
+    whole job).  `device` is where the process group's backend reduces: a CUDA device for NCCL,
+    the CPU for gloo."""
+    if world == 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, t_max):
+    """Whole-job throughput: every rank processes units_per_rank in at most t_max seconds."""
+    return world * units_per_rank / t_max
+
+
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -339,17 +357,10 @@ def gpu_arm(args):
     clocks = clk.summary()
     clocks["window"] = "whole GPU run (warm-up, timed steps, e2e repeat); 100 ms sampling"
 
-    def reduce_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    t_total = reduce_max(float(r["step_ms"].sum()) / 1e3)
-    t_e2e = reduce_max(float(r2["step_ms"].sum()) / 1e3)
+    t_total = reduce_max(float(r["step_ms"].sum()) / 1e3, world, dev)
+    t_e2e = reduce_max(float(r2["step_ms"].sum()) / 1e3, world, dev)
     px_units = H * W * GN_ITERS * args.steps
-    value = world * px_units / t_total
+    value = job_rate(world, px_units, t_total)
     visits_total = float(r["visits"].sum())
     # roofline of the two kernels; the dominant one (larger share of step time) is reported
     hbm, hbm_kind = measured_hbm_peak()
@@ -384,12 +395,12 @@ def gpu_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(n_frames), "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"{world} independent replica(s)", "hash_slots": HASH_SLOTS},
-            "fused_voxels_per_s": world * visits_total / t_total,
+            "fused_voxels_per_s": job_rate(world, visits_total, t_total),
             "track_px_per_s_kernel_only": H * W * GN_ITERS * args.steps / (r["track_ms"].sum() / 1e3),
             "roofline": roof,
             "forms": forms,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * px_units / t_e2e, "unit": "px/s", "h2d_bytes_per_step": H * W * 4,
+            "e2e": {"value": job_rate(world, px_units, t_e2e), "unit": "px/s", "h2d_bytes_per_step": H * W * 4,
                     "d2h_bytes_per_step": 16 * 8},
             "gpu_launches": r["launches"],
             "clocks": clocks,
