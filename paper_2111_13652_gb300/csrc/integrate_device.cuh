@@ -105,18 +105,41 @@ __device__ __forceinline__ long long voxel_index<HashMap>(const HashMap& map, in
 template <>
 __device__ __forceinline__ long long voxel_index<HashMap16>(const HashMap16& map, int mx, int my, int mz,
                                                             BlockCache& bc, int* err, unsigned int* n_new,
-                                                            const int*) {
+                                                            const int* far) {
     const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
     if (bx != bc.bx || by != bc.by || bz != bc.bz) {
-        const long long idx = map.base.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
+        if (bc.fbase >= 0 && bx == bc.fx && by == bc.fy && bz == bc.fz) {
+            bc.base = bc.fbase;
+            bc.fbase = -1;
+        } else {
+            const long long idx = map.base.find_or_insert(bx * 8, by * 8, bz * 8, err, n_new);
+            bc.base = -1;
+            if (idx >= 0) {
+                const int ci = acc_entry(map, idx >> 9, err);
+                if (ci >= 0) bc.base = (long long)ci * kBlockVoxels;
+            }
+            // the far block (found, not inserted) and its frame accumulator entry, as for FP32 maps;
+            // an entry that then receives no sums is read and freed by the apply pass unchanged
+            if (!bc.ahead) {
+                bc.ahead = true;
+                const int fx = floor_div8(far[0]), fy = floor_div8(far[1]), fz = floor_div8(far[2]);
+                if (fx != bx || fy != by || fz != bz) {
+                    const long long fidx = map.base.find(fx * 8, fy * 8, fz * 8);
+                    if (fidx >= 0) {
+                        const int fci = acc_entry(map, fidx >> 9, err);
+                        if (fci >= 0) {
+                            bc.fbase = (long long)fci * kBlockVoxels;
+                            bc.fx = fx;
+                            bc.fy = fy;
+                            bc.fz = fz;
+                        }
+                    }
+                }
+            }
+        }
         bc.bx = bx;
         bc.by = by;
         bc.bz = bz;
-        bc.base = -1;
-        if (idx >= 0) {
-            const int ci = acc_entry(map, idx >> 9, err);
-            if (ci >= 0) bc.base = (long long)ci * kBlockVoxels;
-        }
     }
     if (bc.base < 0) return -1;
     return bc.base + ((mx & 7) + 8 * (my & 7) + 64 * (mz & 7));
