@@ -102,3 +102,17 @@ int main(void) {
     assert G.VOXEL_DTYPE.itemsize == C.sizeof(G.gsdf_voxel) == 32
     assert G.POINT_DTYPE.itemsize == C.sizeof(G.gsdf_point) == 40
     assert G.POINT_DTYPE.fields["p"][1] == G.gsdf_point.p.offset and G.POINT_DTYPE.fields["n"][1] == G.gsdf_point.n.offset
+
+
+def test_gn_update_binding_rejects_bad_tensors_without_gpu(lib_path):
+    """The binding checks device, dtype, contiguity and shape before any library call."""
+    torch = pytest.importorskip("torch")
+    G.load_library(lib_path)
+    n = 3
+    Hb = torch.zeros((n, 27), dtype=torch.float64)
+    nv = torch.zeros(n, dtype=torch.int64)
+    T = torch.eye(4, dtype=torch.float64).repeat(n, 1, 1)
+    with pytest.raises(ValueError, match="Hb"):
+        G.gn_update(Hb, nv, 0.0, T)  # host tensors
+    with pytest.raises(ValueError, match="Hb"):
+        G.gn_update(Hb.float(), nv, 0.0, T)
