@@ -197,6 +197,22 @@ class RoomScene:
             sid = np.where(closer, 6 + len(self.spheres) + k, sid)
         return t, sid
 
+    def normals(self, p, sid):
+        """Unit surface normals (sign irrelevant) at hit points p with surface ids sid."""
+        n = np.zeros_like(p)
+        wall = sid < 6
+        n[wall, sid[wall] // 2] = 1.0
+        ns = len(self.spheres)
+        for k, (c, r) in enumerate(self.spheres):
+            m = sid == 6 + k
+            n[m] = (p[m] - c) / r
+        for k, (blo, bhi) in enumerate(self.boxes):
+            m = np.where(sid == 6 + ns + k)[0]
+            q = p[m]
+            ax = np.argmin(np.minimum(np.abs(q - blo), np.abs(q - bhi)), axis=1)
+            n[m, ax] = 1.0
+        return n
+
     def free_clearance(self, x):
         """Distance from point x to the nearest obstacle surface (positive in free space)."""
         x = np.asarray(x, np.float64)
@@ -451,6 +467,53 @@ def sphere_orbit_poses(n_frames: int, seed: int, radius=0.5, deg_per_frame=1.5) 
     return poses
 
 
+def view_observability(scene: RoomScene, cam: Camera, T_wc: np.ndarray, stride: int = 8) -> float:
+    """Smallest eigenvalue of the mean of n n^T over the surface normals a view sees within the
+    depth range (every stride-th pixel).  A camera position is recoverable from depth along every
+    direction only if the visible normals span 3D; a view of one wall (or of two walls and
+    nothing else) has a value near 0."""
+    dc = cam.ray_dirs_cam().reshape(cam.height, cam.width, 3)[::stride, ::stride].reshape(-1, 3)
+    d = dc @ T_wc[:3, :3].T
+    o = T_wc[:3, 3]
+    t, sid = scene.raycast_id(o, d)
+    ok = np.isfinite(t) & (t > 0) & (t <= cam.depth_max)
+    if not np.any(ok):
+        return 0.0
+    n = scene.normals(o + d[ok] * t[ok, None], sid[ok])
+    return float(np.linalg.eigvalsh(n.T @ n / len(n))[0])
+
+
+def max_turn_deg(poses) -> float:
+    """Largest rotation angle between consecutive camera orientations, in degrees."""
+    worst = 0.0
+    for a, b in zip(poses[:-1], poses[1:]):
+        c = (np.trace(a[:3, :3].T @ b[:3, :3]) - 1.0) / 2.0
+        worst = max(worst, math.degrees(math.acos(min(1.0, max(-1.0, c)))))
+    return worst
+
+
+BATCH_HORIZON = 64  # batch-room trajectories are checked over this many frames
+MIN_OBSERVABILITY = 0.03
+MAX_TURN_DEG = 1.5
+
+
+def batch_room_trajectory(scene: RoomScene, cam: Camera, n_frames: int, seed: int) -> list:
+    """A room trajectory of the batch workload: drawn as room_trajectory does, and re-drawn with
+    the next seed until, over the first max(n_frames, BATCH_HORIZON) frames, the camera turns at
+    most MAX_TURN_DEG per frame and every view has view_observability >= MIN_OBSERVABILITY.
+    The check covers a fixed horizon, so a sequence's first frames do not depend on its length."""
+    horizon = max(n_frames, BATCH_HORIZON)
+    poses = None
+    for attempt in range(256):
+        poses = room_trajectory(scene, horizon, seed + 1_000_003 * attempt)
+        if max_turn_deg(poses) <= MAX_TURN_DEG and all(
+                view_observability(scene, cam, T) >= MIN_OBSERVABILITY for T in poses):
+            break
+    else:
+        raise RuntimeError(f"no well-conditioned trajectory found for seed {seed}")
+    return poses[:n_frames]
+
+
 def batch_scene(index: int, n_frames: int, seed: int = 5) -> BatchScene:
     """Scene `index` of the batch workload: resolution and voxel size cycle with index mod 4;
     index mod 4 == 0 is a dense 64^3 grid around a sphere, the others hashed rooms."""
@@ -465,7 +528,7 @@ def batch_scene(index: int, n_frames: int, seed: int = 5) -> BatchScene:
         dims, origin, slots, damping = (64, 64, 64), (-32, -32, -32), 1, 1e-4
     else:
         scene = make_room(seed * 1000 + index)
-        poses = room_trajectory(scene, n_frames, seed * 1000 + index)
+        poses = batch_room_trajectory(scene, cam, n_frames, seed * 1000 + index)
         dims, origin, damping = None, None, 0.0
         slots = 1 << 13  # 2e6 voxels of capacity at a load factor below 1/2
     depths = np.empty((n_frames, h, w), np.float32)
