@@ -9,9 +9,22 @@ pose.  Frame 0 is fused at its true pose.  The first W frames are warm-up, the n
 value = tracked depth pixels per second per Gauss-Newton iteration over the whole step
         (H*W pixels x 10 iterations x K frames / summed step time);
 fused_voxels_per_s = ray-voxel updates per second over the same time.
+
+Rooflines (HBM, against the measured copy bandwidth) are reported for each kernel with two byte
+counts.  Per access: a tracking step reads 4 B of depth per pixel and, per usable pixel, one 8 B
+block key and the voxel payload (20 B FP32; FP16: 8 B half4 + 4 B W + 4 B block scale; dense grids
+have no key); a fusion reads 4 B of depth per pixel and per ray-voxel update probes a key and
+read-modify-writes 20 B (the payload, or an FP16 map's frame accumulators, whose distinct voxels the
+apply pass then folds).  Compulsory: every distinct voxel and block a pass touches, counted on the
+device by gsdf_footprint, read (tracking) or read and written (fusion) once.
 Inputs (all depth frames) are resident in HBM before timing; L2 is flushed (a 512 MB write)
 between timed steps, outside the timed interval.  e2e repeats the run through the same API
 with each frame copied from pinned host memory and the pose read back inside the interval.
+
+Forms (forms_summary holds their headline figures): 64 scenes batched, 50 timed frames, one
+gsdf_batch_frame graph per frame (FP32 and FP16 payload) against per-scene calls; the room at 4 mm
+for 300 frames with the FP32 and the FP16 payload; the adjoint, bundle adjustment, surface
+extraction and the trilinear baseline tracker.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsdf|reference]
 """
@@ -39,13 +52,6 @@ SEED = 2
 VOXEL = 0.01
 HASH_SLOTS = 1 << 18
 FALLBACK_HBM_GBS = 6800.0
-# algorithmic bytes per unit: tracking reads 4 B of depth per pixel and, for each
-# pixel with a usable voxel, one 8 B key probe and the 20 B payload; fusion reads 4 B of depth per
-# pixel and each ray-voxel update probes an 8 B key and read-modify-writes the 20 B payload.
-TRACK_B_PER_PX = 4
-TRACK_B_PER_VALID = 8 + 20
-INT_B_PER_PX = 4
-INT_B_PER_VISIT = 8 + 2 * 20
 
 
 def workload_name(n_frames):
@@ -174,10 +180,10 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def make_sequence(n_frames):
+def make_sequence(n_frames, processes=1):
     from paper_2111_13652_gb300 import inputs as I
 
-    return I.room_sequence(seed=SEED, n_frames=n_frames, voxel_size=VOXEL)
+    return I.room_sequence(seed=SEED, n_frames=n_frames, voxel_size=VOXEL, processes=processes)
 
 
 # -----------------------------------------------------------------------------------------------
@@ -205,6 +211,87 @@ def run_oracle(seq, first, count):
             visits += st.n_visits
     px = seq.cam.width * seq.cam.height * GN_ITERS * count
     return t_sum, px, visits
+
+
+def _oracle_replica(args):
+    """One single-threaded oracle process of the all-core CPU leg: fuse frame 0 and run the frames
+    before `first`, wait for every replica, then time frames first..first+count-1."""
+    depths, cam, poses, first, count, barrier = args
+    from oracle import oracle as O
+
+    om = O.OracleMap(O.params(VOXEL))
+    om.integrate(depths[0], cam, poses[0])
+    T = poses[0].copy()
+
+    def frame(f, T):
+        for _ in range(GN_ITERS):
+            T, _ = om.track_step(depths[f], cam, T)
+        om.integrate(depths[f], cam, T)
+        return T
+
+    for f in range(1, first):
+        T = frame(f, T)
+    barrier.wait()
+    t0 = time.time()
+    for f in range(first, first + count):
+        T = frame(f, T)
+    return t0, time.time(), cam.width * cam.height * GN_ITERS * count
+
+
+def run_oracle_replicas(seq, first, count, n):
+    """The oracle on every host core at once: n independent replicas of run_oracle's loop in spawned
+    processes, released together; the units of all of them over the span from the first start to
+    the last end."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    k = first + count
+    with ctx.Manager() as mgr:
+        bar = mgr.Barrier(n)
+        job = (seq.depths[:k], seq.cam, [np.asarray(T) for T in seq.poses[:k]], first, count, bar)
+        with cf.ProcessPoolExecutor(n, mp_context=ctx) as ex:
+            res = list(ex.map(_oracle_replica, [job] * n))
+    span = max(r[1] for r in res) - min(r[0] for r in res)
+    return sum(r[2] for r in res) / span
+
+
+def forms_summary(forms):
+    """The headline figures of every form, kept short so that they appear early in the line."""
+    out = {}
+    b = forms.get("batched_64_scenes")
+    if b:
+        sp = b["split"]
+        out["batched_64_scenes"] = {
+            "px_per_s": b["value"], "fp16_px_per_s": b["fp16_value"], "plain_px_per_s": b["plain_value"],
+            "ms_per_frame": b["ms_per_frame"], "speedup_vs_plain": b["speedup_vs_plain"],
+            "fp16_speedup_vs_plain": b["fp16_speedup_vs_plain"],
+            "max_pose_error_in_voxels": {k: b["pose_accuracy"][k]["max_in_voxels"]
+                                         for k in ("batched", "batched_fp16", "plain")},
+            "accuracy_gate": b["pose_accuracy"]["gate_all_scenes_within_2_voxels"],
+            "hbm_frac": {m: {k: {"per_access": sp[m][k]["per_access"]["frac"],
+                                 "compulsory": sp[m][k]["compulsory"]["frac"]} for k in ("track", "fusion")}
+                         for m in sp}}
+    f = forms.get("fp16_payload_4mm")
+    if f:
+        last = str(FP16_FRAMES)
+        out["fp16_payload_4mm"] = {
+            "ms_per_frame": {m: f[m]["ms_per_frame"] for m in ("fp32", "fp16")},
+            "voxels": f["fp16"]["voxels"],
+            "pose_error_m_at_300": {m: f[m]["pose_error_m"][last] for m in ("fp32", "fp16")},
+            "fp16_vs_fp32_at_300": {k: f["checkpoints"][last]["fields_fp16_vs_fp32"][k]
+                                    for k in ("max_dpsi", "max_dghat")},
+            "hbm_frac": {m: {k: {"per_access": f[m]["roofline"][k]["per_access"]["frac"],
+                                 "compulsory": f[m]["roofline"][k]["compulsory"]["frac"]} for k in ("track", "fusion")}
+                         for m in ("fp32", "fp16")}}
+    a = forms.get("adjoint_10_keyframes")
+    if a:
+        out["adjoint_10_keyframes"] = {"gradient_evaluations_per_s": a["gradient_evaluations_per_s"],
+                                       "hbm_frac": a["hbm_frac_energy_and_gradient"]}
+    t = forms.get("taylor_vs_trilinear_room640")
+    if t:
+        out["taylor_vs_trilinear"] = {"tracking_speedup": t["tracking_speedup_taylor_vs_trilinear"]}
+    return out
 
 
 def reference_arm(args):
@@ -238,25 +325,27 @@ def gpu_arm(args):
     from paper_2111_13652_gb300 import gsdf as G
 
     rank, world, local = dist_env()
+    procs = max(1, min(16, os.cpu_count() or 1))
     batch_scenes = None
     if not args.no_batch_form:
         from paper_2111_13652_gb300 import inputs as I
 
         # ray-cast the batch workload in a spawned pool before the first CUDA call
-        batch_scenes = I.batch_scenes(BATCH_SCENES, 1 + BATCH_WARMUP + BATCH_STEPS,
-                                      processes=max(1, min(16, os.cpu_count() or 1)))
+        batch_scenes = I.batch_scenes(BATCH_SCENES, 1 + BATCH_WARMUP + BATCH_STEPS, processes=procs)
     fp16_seq = None
     if not args.no_fp16_form:
         from paper_2111_13652_gb300 import inputs as I
 
-        # the 4 mm room: the same path at the pace of a 300-frame sequence (0.5 cm per frame)
-        fp16_seq = I.room_sequence(seed=SEED, n_frames=1 + FP16_WARMUP + FP16_STEPS, voxel_size=FP16_VOXEL,
-                                   frames_per_segment=75)
+        # the 4 mm room: 300 frames at 0.5 cm per frame
+        fp16_seq = I.room_sequence(seed=SEED, n_frames=1 + FP16_FRAMES, voxel_size=FP16_VOXEL,
+                                   frames_per_segment=75, processes=procs)
     keyframes = None
     if not args.no_adjoint_form:
         from paper_2111_13652_gb300 import inputs as I
 
         keyframes = I.keyframes(seed=SEED, n_keyframes=ADJ_KEYFRAMES, stride=ADJ_STRIDE, voxel_size=VOXEL)
+    n_frames = max(100, 1 + args.warmup + args.steps)
+    seq = make_sequence(n_frames, procs)
     if world > 1:
         import torch.distributed as dist
 
@@ -264,8 +353,6 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     G.load_library()
-    n_frames = max(100, 1 + args.warmup + args.steps)
-    seq = make_sequence(n_frames)
     H, W = seq.cam.height, seq.cam.width
     K = G.intrinsics(seq.cam)
     stream = torch.cuda.current_stream(dev)
@@ -334,18 +421,22 @@ def gpu_arm(args):
         visits = np.array([G.integrate_stats_from_bytes(ist[k]).n_visits for k in range(args.steps)])
         blocks = G.integrate_stats_from_bytes(ist[-1]).n_blocks_total
         final_pose = pose.cpu().numpy()
+        # distinct voxels and blocks of the last frame's tracking and fusion (compulsory bytes)
+        fp_t = m.footprint(G.GSDF_FOOTPRINT_TRACK, dbuf, K, pose)
+        fp_f = m.footprint(G.GSDF_FOOTPRINT_FUSE, dbuf, K, pose)
         m.close()
         return dict(step_ms=step_ms, track_ms=track_ms, int_ms=int_ms, n_valid=n_valid, visits=visits,
-                    blocks=blocks, wall=wall, launches=launches, pose=final_pose)
+                    blocks=blocks, wall=wall, launches=launches, pose=final_pose, fp_t=fp_t, fp_f=fp_f)
 
     with ClockSampler(local) as clk:
         r = run(e2e=False)
         r2 = run(e2e=True)
         forms = {}
+        hbm = measured_hbm_peak()[0]
         if batch_scenes is not None:
-            forms["batched_64_scenes"] = batch_form(G, torch, dev, stream, batch_scenes)
+            forms["batched_64_scenes"] = batch_form(G, torch, dev, stream, batch_scenes, hbm)
         if not args.no_fp16_form:
-            forms["fp16_payload_4mm"] = fp16_form(G, torch, dev, stream, fp16_seq)
+            forms["fp16_payload_4mm"] = fp16_form(G, torch, dev, stream, fp16_seq, hbm)
         if keyframes is not None:
             forms["adjoint_10_keyframes"] = adjoint_form(G, torch, dev, stream, keyframes, measured_hbm_peak()[0])
             if not args.no_ba_form:
@@ -364,22 +455,33 @@ def gpu_arm(args):
     visits_total = float(r["visits"].sum())
     # roofline of the two kernels; the dominant one (larger share of step time) is reported
     hbm, hbm_kind = measured_hbm_peak()
-    track_bytes = TRACK_B_PER_PX * H * W + TRACK_B_PER_VALID * r["n_valid"]  # per launch
-    track_gbs = float(track_bytes.sum() / (r["track_ms"].sum() / 1e3) / 1e9)  # 10 launches per interval
-    int_bytes = INT_B_PER_PX * H * W + INT_B_PER_VISIT * r["visits"]
-    int_gbs = float(int_bytes.sum() / (r["int_ms"].sum() / 1e3) / 1e9)
+    track_b = track_bytes("f32", H * W, r["n_valid"])  # per launch (per access)
+    track_gbs = float(track_b.sum() / (r["track_ms"].sum() / 1e3) / 1e9)  # 10 launches per interval
+    int_b = fuse_bytes("f32", H * W, r["visits"])
+    int_gbs = float(int_b.sum() / (r["int_ms"].sum() / 1e3) / 1e9)
+    step_s = float(r["track_ms"].mean()) / 1e3 / GN_ITERS
+    fuse_s = float(r["int_ms"].mean()) / 1e3
     share_track = float(r["track_ms"].sum() / r["step_ms"].sum())  # the rest: staging copy
     share_int = float(r["int_ms"].sum() / r["step_ms"].sum())
     if share_int >= share_track:
         dom, ach, traffic = "integrate_kernel", int_gbs, profiled_traffic("integrate_kernel")
     else:
         dom, ach, traffic = "track_kernel", track_gbs, profiled_traffic("track_kernel")
-    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "kernel": dom, "peak_source": hbm_kind,
+            "bytes": "per access (algorithmic): tracking 4 B of depth per pixel + 28 B (8 B key probe + 20 B "
+                     "payload) per usable pixel; fusion 4 B per pixel + 48 B (key + 20 B read-modify-write) per "
+                     "ray-voxel update",
             "kernels": {"track_kernel": {"GBs": track_gbs, "share": share_track,
-                                         "us_per_launch": 1e3 * float(r["track_ms"].mean()) / GN_ITERS},
+                                         "us_per_launch": 1e6 * step_s,
+                                         "compulsory": roof(track_bytes("f32", H * W, 0, *r["fp_t"]), step_s, hbm),
+                                         "distinct_voxels": r["fp_t"][0]},
                         "integrate_kernel": {"GBs": int_gbs, "share": share_int,
-                                             "us_per_launch": 1e3 * float(r["int_ms"].mean())}}}
+                                             "us_per_launch": 1e6 * fuse_s,
+                                             "compulsory": roof(fuse_bytes("f32", H * W, 0, *r["fp_f"]), fuse_s, hbm),
+                                             "distinct_voxels": r["fp_f"][0]}},
+            "l2_note": "a 640x480 frame's tracking and fusion working set (a few MB) is L2-resident after the "
+                       "first Gauss-Newton step; see forms.*.split / roofline for the batched and 4 mm forms"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         first_cpu, count = 1, 3
@@ -387,6 +489,12 @@ def gpu_arm(args):
         cpu = {"value": px_cpu / t_cpu, "unit": "px/s", "cores": 1, "kind": "oracle",
                "sample": f"frames {first_cpu}..{first_cpu + count - 1} of the same sequence "
                          f"({GN_ITERS} GN steps + fusion each), single-threaded"}
+        ncores = os.cpu_count() or 1
+        v_all = run_oracle_replicas(seq, first_cpu, count, ncores)
+        cpu["all_cores"] = {"value": v_all, "unit": "px/s", "cores": ncores, "kind": "oracle",
+                            "sample": f"{ncores} independent single-threaded oracle processes (one per host "
+                                      f"core), each on frames {first_cpu}..{first_cpu + count - 1}; "
+                                      f"units of all of them over the slowest one's time"}
     if rank == 0:
         gt = seq.poses[first + n_steps_total - 1]
         line = {
@@ -397,7 +505,8 @@ def gpu_arm(args):
                        "parallelism": f"{world} independent replica(s)", "hash_slots": HASH_SLOTS},
             "fused_voxels_per_s": job_rate(world, visits_total, t_total),
             "track_px_per_s_kernel_only": H * W * GN_ITERS * args.steps / (r["track_ms"].sum() / 1e3),
-            "roofline": roof,
+            "roofline": roofline,
+            "forms_summary": forms_summary(forms),
             "forms": forms,
             "cpu_baseline": cpu,
             "e2e": {"value": job_rate(world, px_units, t_e2e), "unit": "px/s", "h2d_bytes_per_step": H * W * 4,
@@ -415,7 +524,45 @@ def gpu_arm(args):
 
 BATCH_SCENES = 64
 BATCH_WARMUP = 3
-BATCH_STEPS = 5
+BATCH_STEPS = 50
+BATCH_SPLIT_STEPS = 10
+
+# bytes a tracking step and a fusion read or write, per unit, by payload kind ("dense", "f32",
+# "f16"); see the roofline paragraphs of the module docstring
+SLOT_B = {"dense": 0, "f32": 8, "f16": 8}       # the 8 B block key probed per lookup
+PAYLOAD_B = {"dense": 20, "f32": 20, "f16": 16}  # per lookup: float4 + W (FP16: half4 + W + block scale)
+VOXEL_B = {"dense": 20, "f32": 20, "f16": 12}    # per distinct voxel (FP16: half4 + W)
+BLOCK_B = {"dense": 0, "f32": 8, "f16": 12}      # per distinct block (key; FP16 also its scale)
+
+
+def track_bytes(kind, n_px, n_valid, vox=None, blocks=None):
+    """One tracking step: per access (4 B of depth per pixel, one key probe and one payload read per
+    usable pixel) or, given the distinct voxels and blocks, compulsory (each read once)."""
+    if vox is None:
+        return 4 * n_px + (SLOT_B[kind] + PAYLOAD_B[kind]) * n_valid
+    return 4 * n_px + VOXEL_B[kind] * vox + BLOCK_B[kind] * blocks
+
+
+def fuse_bytes(kind, n_px, visits, vox=None, blocks=None):
+    """One fusion: per access (4 B of depth per pixel; per ray-voxel update one key probe and a
+    20 B read-modify-write of the FP32 payload or, for FP16 maps, of the frame accumulators, whose
+    distinct voxels are then folded: sums read and cleared, payload read and written) or compulsory
+    (each distinct voxel's payload read and written once, each block's key once)."""
+    if vox is None:
+        b = 4 * n_px + (8 + 40) * visits
+        return b
+    return 4 * n_px + 2 * VOXEL_B[kind] * vox + BLOCK_B[kind] * blocks
+
+
+def fp16_apply_bytes(vox, blocks):
+    """The FP16 apply pass per access: each listed block's 512 weight sums, and per distinct voxel
+    its sums (read 20 B, cleared 20 B) and payload (read and written, 12 B each)."""
+    return 4 * 512 * blocks + (20 + 20 + 12 + 12) * vox
+
+
+def roof(bytes_per_unit, seconds_per_unit, peak):
+    gbs = bytes_per_unit / seconds_per_unit / 1e9
+    return {"GBs": gbs, "frac": gbs / peak}
 
 
 def observable(sc, T):
@@ -425,114 +572,196 @@ def observable(sc, T):
     return T[:3, :3].T @ (-T[:3, 3]) if sc.dense_dims is not None else T[:3, 3]
 
 
-def batch_form(G, torch, dev, stream, scenes):
-    """64 independent scenes (160x120..640x480, dense 64^3 and hashed rooms, 1-4 cm voxels): each
-    frame runs 10 Gauss-Newton steps and fusion of every scene, batched (persistent launches,
-    graph-replayed tracking, autotuned tiles) and, for comparison, through plain per-scene calls."""
+def batch_form(G, torch, dev, stream, scenes, hbm):
+    """64 independent scenes (160x120..640x480, dense 64^3 spheres and hashed rooms, 1-4 cm voxels):
+    each frame runs 10 Gauss-Newton steps and fusion of every scene.  Batched: one gsdf_batch_frame
+    per frame (one CUDA graph: persistent tracking launches, persistent fusion, depth pointers
+    advanced on the device), with the FP32 payload and with the rooms in FP16; plain: per-scene
+    calls.  A split run times the batched tracking and fusion kernels apart for their rooflines."""
     n = len(scenes)
     Ks = [G.intrinsics(sc.cam) for sc in scenes]
-    depths = [torch.from_numpy(sc.depths).to(dev) for sc in scenes]
+    depths = [torch.from_numpy(sc.depths).to(dev) for sc in scenes]  # (F, H, W) per scene, in HBM
+    n_px = [sc.cam.width * sc.cam.height for sc in scenes]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    last = BATCH_WARMUP + BATCH_STEPS
 
-    def make_maps():
+    def kinds(fp16):
+        return ["dense" if sc.dense_dims is not None else ("f16" if fp16 else "f32") for sc in scenes]
+
+    def make_maps(fp16):
         maps = []
         for sc in scenes:
             if sc.dense_dims is not None:
                 cfg = G.make_config(sc.voxel_size, dense_dims=sc.dense_dims, dense_origin=sc.dense_origin,
                                     damping=sc.damping)
             else:
-                cfg = G.make_config(sc.voxel_size, hash_slots=sc.hash_slots, damping=sc.damping)
+                cfg = G.make_config(sc.voxel_size, hash_slots=sc.hash_slots, damping=sc.damping, fp16=fp16,
+                                    max_touched_blocks=sc.hash_slots // 2)
             maps.append(G.Map(cfg, stream))
         return maps
 
-    px_per_iter = sum(sc.cam.width * sc.cam.height for sc in scenes)
+    px_per_iter = sum(n_px)
     out = {}
-    for mode in ("batched", "plain"):
-        maps = make_maps()
+    for mode in ("batched", "batched_fp16", "plain"):
+        maps = make_maps(mode == "batched_fp16")
         poses = [torch.from_numpy(np.ascontiguousarray(sc.poses[0])).to(dev) for sc in scenes]
         istats = torch.zeros((n, G.INTEGRATE_STATS_BYTES), dtype=torch.uint8, device=dev)
-        batch = G.Batch(maps, stream) if mode == "batched" else None
-        staging = [torch.empty_like(d[0]) for d in depths]
-        tiles = None
-        times, visits = [], 0
-        for f in range(1 + BATCH_WARMUP + BATCH_STEPS):
-            frame = [d[f] for d in depths]
+        ist_all = torch.zeros((BATCH_STEPS, n, G.INTEGRATE_STATS_BYTES), dtype=torch.uint8, device=dev)
+        batch, tiles = None, None
+        if mode != "plain":
+            batch = G.Batch(maps, stream)
+            batch.set_frames([d[0] for d in depths], Ks, poses, integrate_stats=istats)
+            batch.set_depth_stride(n_px)
+            batch.frame(0)  # frame 0 fused at its true pose; the depth pointers now sit at frame 1
+            tiles = batch.autotune()  # untimed: tile size and CTAs per SM for these frame sizes
+        else:
+            staging = [torch.empty_like(d[0]) for d in depths]
+            for s in range(n):
+                maps[s].integrate(depths[s][0], Ks[s], poses[s])
+        ev = []
+        for f in range(1, last + 1):
             timed = f > BATCH_WARMUP
             if timed:
-                flush.fill_(f & 0xFF)
+                flush.fill_(f & 0xFF)  # evict L2 (not timed)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            if mode == "batched":
-                batch.set_frames(frame, Ks, poses, integrate_stats=istats)
-                if f > 0:
-                    batch.track(GN_ITERS)
-                batch.integrate()
+            if batch is not None:
+                batch.frame(GN_ITERS)
             else:  # each scene through its own handle; a staging buffer keeps gsdf_track a graph replay
                 for s in range(n):
-                    staging[s].copy_(frame[s], non_blocking=True)
-                    if f > 0:
-                        maps[s].track(staging[s], Ks[s], poses[s], GN_ITERS)
+                    staging[s].copy_(depths[s][f], non_blocking=True)
+                    maps[s].track(staging[s], Ks[s], poses[s], GN_ITERS)
                     maps[s].integrate(staging[s], Ks[s], poses[s], istats[s])
             if timed:
                 e1.record(stream)
-                times.append(e1)
-                times.append(e0)
-            if f == 0 and mode == "batched":
-                tiles = batch.autotune()  # untimed: picks tile size and CTAs per SM on these frames
-            if timed:
-                torch.cuda.synchronize(dev)
-                ist = istats.cpu().numpy()
-                visits += sum(G.integrate_stats_from_bytes(ist[s]).n_visits for s in range(n))
+                ev.append((e0, e1))
+                ist_all[f - 1 - BATCH_WARMUP].copy_(istats)
         torch.cuda.synchronize(dev)
-        ms = sum(times[i + 1].elapsed_time(times[i]) for i in range(0, len(times), 2))
+        ms = float(sum(a.elapsed_time(b) for a, b in ev))
+        ist = ist_all.cpu().numpy()
+        visits = sum(G.integrate_stats_from_bytes(ist[k, s]).n_visits for k in range(BATCH_STEPS) for s in range(n))
         final = [p.cpu().numpy() for p in poses]
-        err = [float(np.linalg.norm(observable(sc, T) - observable(sc, sc.poses[BATCH_WARMUP + BATCH_STEPS])))
-               for sc, T in zip(scenes, final)]
-        out[mode] = dict(ms=ms, visits=visits, final=final, err=err, tiles=tiles)
-        for m in maps:
-            m.sync()
+        err = [float(np.linalg.norm(observable(sc, T) - observable(sc, sc.poses[last]))) for sc, T in zip(scenes, final)]
+        status = [int(G.gsdf_sync(m.h)) for m in maps]
+        out[mode] = dict(ms=ms, visits=visits, final=final, err=err, tiles=tiles, status=status)
         if batch is not None:
             batch.close()
         for m in maps:
             m.close()
-    b, pl = out["batched"], out["plain"]
-    pose_diff = max(float(np.linalg.norm(observable(sc, x) - observable(sc, y)))
-                    for sc, x, y in zip(scenes, b["final"], pl["final"]))
+    b, b16, pl = out["batched"], out["batched_fp16"], out["plain"]
+
+    # split run: the batched tracking and fusion kernels timed apart, for their rooflines
+    split = {}
+    for mode in ("batched", "batched_fp16"):
+        fp16 = mode == "batched_fp16"
+        maps = make_maps(fp16)
+        poses = [torch.from_numpy(np.ascontiguousarray(sc.poses[0])).to(dev) for sc in scenes]
+        tstats = torch.zeros((n, G.TRACK_STATS_BYTES), dtype=torch.uint8, device=dev)
+        istats = torch.zeros((n, G.INTEGRATE_STATS_BYTES), dtype=torch.uint8, device=dev)
+        batch = G.Batch(maps, stream)
+        batch.set_frames([d[0] for d in depths], Ks, poses, tstats, istats)
+        batch.integrate()
+        batch.autotune()
+        t_track, t_fuse, valid, visits = 0.0, 0.0, [], []
+        for f in range(1, 1 + BATCH_WARMUP + BATCH_SPLIT_STEPS):
+            batch.set_frames([d[f] for d in depths], Ks, poses, tstats, istats)
+            flush.fill_(f & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            batch.track(GN_ITERS)
+            e[1].record(stream)
+            batch.integrate()
+            e[2].record(stream)
+            torch.cuda.synchronize(dev)
+            if f > BATCH_WARMUP:
+                t_track += e[0].elapsed_time(e[1]) / 1e3
+                t_fuse += e[1].elapsed_time(e[2]) / 1e3
+                ts, ist = tstats.cpu().numpy(), istats.cpu().numpy()
+                # per-step usable pixels: the last step's count (the count barely moves over the steps)
+                valid += [G.track_stats_from_bytes(ts[s]).n_valid for s in range(n)]
+                visits += [G.integrate_stats_from_bytes(ist[s]).n_visits for s in range(n)]
+        # distinct voxels and blocks of the last frame (compulsory bytes), per scene
+        fl = BATCH_WARMUP + BATCH_SPLIT_STEPS
+        fp_t = [maps[s].footprint(G.GSDF_FOOTPRINT_TRACK, depths[s][fl], Ks[s], poses[s]) for s in range(n)]
+        fp_f = [maps[s].footprint(G.GSDF_FOOTPRINT_FUSE, depths[s][fl], Ks[s], poses[s]) for s in range(n)]
+        batch.close()
+        for m in maps:
+            m.close()
+        kd = kinds(fp16)
+        k_steps = BATCH_SPLIT_STEPS
+        valid_mean = np.sum(np.reshape(valid, (k_steps, n)), axis=0) / k_steps
+        visits_mean = np.sum(np.reshape(visits, (k_steps, n)), axis=0) / k_steps
+        tb_acc = sum(track_bytes(kd[s], n_px[s], valid_mean[s]) for s in range(n))
+        tb_cmp = sum(track_bytes(kd[s], n_px[s], 0, *fp_t[s]) for s in range(n))
+        fb_acc = sum(fuse_bytes(kd[s], n_px[s], visits_mean[s]) for s in range(n))
+        fb_acc += sum(fp16_apply_bytes(*fp_f[s]) for s in range(n) if kd[s] == "f16")
+        fb_cmp = sum(fuse_bytes(kd[s], n_px[s], 0, *fp_f[s]) for s in range(n))
+        step_s = t_track / (k_steps * GN_ITERS)
+        fuse_s = t_fuse / k_steps
+        split[mode] = {
+            "track": {"kernel": "batch_track_kernel", "us_per_step": 1e6 * step_s,
+                      "bytes_per_step": {"per_access": tb_acc, "compulsory": tb_cmp},
+                      "per_access": roof(tb_acc, step_s, hbm), "compulsory": roof(tb_cmp, step_s, hbm),
+                      "distinct_voxels": int(sum(x[0] for x in fp_t)), "usable_px": float(np.sum(valid_mean))},
+            "fusion": {"kernel": "batch_integrate_kernel" + (" + batch_list16/apply16" if fp16 else ""),
+                       "us_per_frame": 1e6 * fuse_s,
+                       "bytes_per_frame": {"per_access": fb_acc, "compulsory": fb_cmp},
+                       "per_access": roof(fb_acc, fuse_s, hbm), "compulsory": roof(fb_cmp, fuse_s, hbm),
+                       "distinct_voxels": int(sum(x[0] for x in fp_f)), "visits": float(np.sum(visits_mean))},
+        }
+
+    def acc(r):
+        e = np.array(r["err"])
+        vs = np.array([sc.voxel_size for sc in scenes])
+        worst = int(np.argmax(e / vs))
+        return {"mean_m": float(e.mean()), "max_m": float(e.max()), "max_in_voxels": float((e / vs).max()),
+                "worst_scene": worst, "scenes_over_2_voxels": int(np.sum(e > 2 * vs)),
+                "per_scene_m": [round(x, 5) for x in e.tolist()]}
+
+    def diff(x, y):
+        return max(float(np.linalg.norm(observable(sc, p) - observable(sc, q)))
+                   for sc, p, q in zip(scenes, x["final"], y["final"]))
+
+    units = px_per_iter * GN_ITERS * BATCH_STEPS
+    a_b, a_16, a_pl = acc(b), acc(b16), acc(pl)
     return {
         "workload": f"{n} scenes: 160x120/320x240/480x360/640x480 by index mod 4, dense 64^3 sphere grid "
-                    f"(index mod 4 = 0) or hashed room, voxels 1-4 cm; per frame {GN_ITERS} GN steps + "
-                    f"fusion of every scene; {BATCH_WARMUP} warm-up frames, {BATCH_STEPS} timed",
-        "value": px_per_iter * GN_ITERS * BATCH_STEPS / (b["ms"] / 1e3), "unit": "px/s",
-        "ms_per_frame": b["ms"] / BATCH_STEPS,
+                    f"(index mod 4 = 0) or hashed room, voxels 1-4 cm; per frame {GN_ITERS} GN steps + fusion of "
+                    f"every scene; frame 0 fused at its true pose, {BATCH_WARMUP} warm-up frames, {BATCH_STEPS} "
+                    f"timed; L2 flushed before every timed frame",
+        "value": units / (b["ms"] / 1e3), "unit": "px/s", "ms_per_frame": b["ms"] / BATCH_STEPS,
         "fused_voxels_per_s": b["visits"] / (b["ms"] / 1e3),
-        "plain_value": px_per_iter * GN_ITERS * BATCH_STEPS / (pl["ms"] / 1e3),
-        "plain_ms_per_frame": pl["ms"] / BATCH_STEPS,
-        "speedup_vs_plain": pl["ms"] / b["ms"],
+        "fp16_value": units / (b16["ms"] / 1e3), "fp16_ms_per_frame": b16["ms"] / BATCH_STEPS,
+        "plain_value": units / (pl["ms"] / 1e3), "plain_ms_per_frame": pl["ms"] / BATCH_STEPS,
+        "speedup_vs_plain": pl["ms"] / b["ms"], "fp16_speedup_vs_plain": pl["ms"] / b16["ms"],
+        "graph": "one gsdf_batch_frame (one CUDA graph launch) per frame",
         "autotuned": {"tile_px": b["tiles"][0], "ctas_per_sm": b["tiles"][1]},
         "pose_accuracy": {
-            "measure": "camera position for rooms; camera-frame sphere centre for sphere-only scenes "
-                       "(rotations about the sphere are unobservable); metres, after the last timed frame",
-            "max_diff_batched_vs_plain": pose_diff,
-            "mean_error_vs_truth": {"batched": float(np.mean(b["err"])), "plain": float(np.mean(pl["err"]))},
-            "max_error_vs_truth": {"batched": float(np.max(b["err"])), "plain": float(np.max(pl["err"]))}},
-        "l2": "flushed before every timed frame",
+            "measure": "camera position for rooms; camera-frame sphere centre for sphere-only scenes (rotations "
+                       "about the sphere are unobservable); metres, after the last timed frame",
+            "batched": a_b, "batched_fp16": a_16, "plain": a_pl,
+            "max_diff_batched_vs_plain": diff(b, pl), "max_diff_fp16_vs_fp32": diff(b16, b),
+            "gate_all_scenes_within_2_voxels": a_b["scenes_over_2_voxels"] == 0 and a_16["scenes_over_2_voxels"] == 0},
+        "map_status": {"batched": max(b["status"]), "batched_fp16": max(b16["status"]), "plain": max(pl["status"])},
+        "split": split,
     }
 
 
-FP16_WARMUP = 3
-FP16_STEPS = 12
 FP16_VOXEL = 0.004
 FP16_SLOTS = 1 << 17
+FP16_FRAMES = 300
+FP16_CHECKS = (1, 10, 100, 300)
 
 
-def fp16_form(G, torch, dev, stream, seq):
-    """The room at 4 mm voxels (T = 2 cm): the per-frame loop with the FP32 payload and with the
-    FP16 payload (per-block scale), same frames, same timing rules."""
+def fp16_form(G, torch, dev, stream, seq, hbm):
+    """The room at 4 mm voxels (T = 2 cm), 300 frames at 0.5 cm per frame: the per-frame loop with the
+    FP32 payload and with the FP16 payload (per-block scale), same frames, same timing rules; pose
+    errors at frames 1, 10, 100 and 300, and the FP16 fields against the FP32 fields there."""
     K = G.intrinsics(seq.cam)
     H, W = seq.cam.height, seq.cam.width
     depths = torch.from_numpy(seq.depths).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    out = {}
+    out, fields, poses_at = {}, {}, {}
     for mode in ("fp32", "fp16"):
         m = G.Map(G.make_config(FP16_VOXEL, hash_slots=FP16_SLOTS, fp16=(mode == "fp16"),
                                 max_touched_blocks=FP16_SLOTS // 2), stream)
@@ -540,43 +769,89 @@ def fp16_form(G, torch, dev, stream, seq):
         dbuf = torch.empty((H, W), dtype=torch.float32, device=dev)
         dbuf.copy_(depths[0])
         m.integrate(dbuf, K, pose)
+        tstats = m.new_track_stats(GN_ITERS)
+        istats = m.new_integrate_stats()
+        valid = torch.zeros(FP16_FRAMES, dtype=torch.int64, device=dev)
+        visits = torch.zeros(FP16_FRAMES, dtype=torch.int64, device=dev)
         ev = []
-        for f in range(1, 1 + FP16_WARMUP + FP16_STEPS):
-            timed = f > FP16_WARMUP
-            if timed:
-                flush.fill_(f & 0xFF)
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                e[0].record(stream)
+        fields[mode], poses_at[mode] = {}, {}
+        for f in range(1, FP16_FRAMES + 1):
+            flush.fill_(f & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
             dbuf.copy_(depths[f], non_blocking=True)
-            m.track(dbuf, K, pose, GN_ITERS)
-            if timed:
-                e[1].record(stream)
-            m.integrate(dbuf, K, pose)
-            if timed:
-                e[2].record(stream)
-                ev.append(e)
+            m.track(dbuf, K, pose, GN_ITERS, tstats)
+            e[1].record(stream)
+            m.integrate(dbuf, K, pose, istats)
+            e[2].record(stream)
+            ev.append(e)
+            valid[f - 1] = tstats[GN_ITERS - 1].view(torch.int64)[28]  # n_valid of the last step
+            visits[f - 1] = istats.view(torch.int64)[1]
+            if f in FP16_CHECKS:  # untimed: pose and fields at the checkpoint
+                torch.cuda.synchronize(dev)
+                poses_at[mode][f] = pose.cpu().numpy()
+                v = m.extract()
+                fields[mode][f] = v
         torch.cuda.synchronize(dev)
         st = G.gsdf_sync(m.h)
-        T = pose.cpu().numpy()
-        gt = seq.poses[FP16_WARMUP + FP16_STEPS]
+        fp_t = m.footprint(G.GSDF_FOOTPRINT_TRACK, dbuf, K, pose)
+        fp_f = m.footprint(G.GSDF_FOOTPRINT_FUSE, dbuf, K, pose)
+        t_frame = np.array([e[0].elapsed_time(e[2]) for e in ev]) / 1e3
+        t_track = np.array([e[0].elapsed_time(e[1]) for e in ev]) / 1e3
+        t_fuse = np.array([e[1].elapsed_time(e[2]) for e in ev]) / 1e3
+        kind = "f16" if mode == "fp16" else "f32"
+        nv, nvis = valid.cpu().numpy(), visits.cpu().numpy()
+        # the last 100 frames (the map at its full size) for the rooflines
+        sl = slice(FP16_FRAMES - 100, FP16_FRAMES)
+        step_s = float(t_track[sl].mean()) / GN_ITERS
+        fuse_s = float(t_fuse[sl].mean())
+        tb_acc = track_bytes(kind, H * W, float(nv[sl].mean()))
+        tb_cmp = track_bytes(kind, H * W, 0, *fp_t)
+        fb_acc = fuse_bytes(kind, H * W, float(nvis[sl].mean())) + (fp16_apply_bytes(*fp_f) if kind == "f16" else 0)
+        fb_cmp = fuse_bytes(kind, H * W, 0, *fp_f)
         out[mode] = {
-            "ms_per_frame": float(np.mean([e[0].elapsed_time(e[2]) for e in ev])),
-            "track_us_per_step": 1e3 * float(np.mean([e[0].elapsed_time(e[1]) for e in ev])) / GN_ITERS,
-            "integrate_us": 1e3 * float(np.mean([e[1].elapsed_time(e[2]) for e in ev])),
-            "voxels": 0, "blocks": m.num_blocks(),
-            "payload_bytes_per_voxel": 12 if mode == "fp16" else 20,
-            "pose_error_m": float(np.linalg.norm(T[:3, 3] - gt[:3, 3])), "status": int(st),
+            "ms_per_frame": 1e3 * float(t_frame.mean()),
+            "track_us_per_step": 1e6 * step_s,
+            "integrate_us": 1e6 * float(t_fuse.mean()),
+            "voxels": int(len(fields[mode][FP16_FRAMES])), "blocks": m.num_blocks(),
+            "payload_bytes_per_voxel": VOXEL_B[kind],
+            "pose_error_m": {str(c): float(np.linalg.norm(poses_at[mode][c][:3, 3] - seq.poses[c][:3, 3]))
+                             for c in FP16_CHECKS},
+            "status": int(st),
+            "roofline": {
+                "track": {"us_per_step": 1e6 * step_s, "per_access": roof(tb_acc, step_s, hbm),
+                          "compulsory": roof(tb_cmp, step_s, hbm), "distinct_voxels": fp_t[0]},
+                "fusion": {"us_per_frame": 1e6 * fuse_s, "per_access": roof(fb_acc, fuse_s, hbm),
+                           "compulsory": roof(fb_cmp, fuse_s, hbm), "distinct_voxels": fp_f[0]},
+                "window": "frames 201..300 (the map at full size); bytes from the last frame's counts"},
         }
-        out[mode]["voxels"] = int(len(m.extract()))
-        out[mode]["final_pose"] = T
         m.close()
-    diff = float(np.abs(out["fp16"].pop("final_pose") - out["fp32"].pop("final_pose")).max())
+
+    def field_diff(a, b):
+        ka = {tuple(x): i for i, x in enumerate(a["m"])}
+        ib, ia = [], []
+        for j, x in enumerate(b["m"]):
+            i = ka.get(tuple(x))
+            if i is not None:
+                ia.append(i)
+                ib.append(j)
+        ga = a["g"][ia].astype(np.float64)
+        gb = b["g"][ib].astype(np.float64)
+        gh = lambda g: g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-30)  # noqa: E731
+        dpsi = np.abs(a["psi"][ia].astype(np.float64) - b["psi"][ib])
+        dg = np.abs(gh(ga) - gh(gb)).max(axis=1)
+        return {"common_voxels": len(ia), "only_fp32": len(a) - len(ia), "only_fp16": len(b) - len(ib),
+                "max_dpsi": float(dpsi.max()), "mean_dpsi": float(dpsi.mean()),
+                "max_dghat": float(dg.max()), "mean_dghat": float(dg.mean())}
+
+    checks = {}
+    for c in FP16_CHECKS:
+        checks[str(c)] = {"pose_diff_fp16_vs_fp32": float(np.abs(poses_at["fp16"][c] - poses_at["fp32"][c]).max()),
+                          "fields_fp16_vs_fp32": field_diff(fields["fp32"][c], fields["fp16"][c])}
     return {
-        "workload": f"hashed room at 4 mm voxels (T = 2 cm), 640x480, trajectory of the 300-frame pace "
-                    f"(0.5 cm/frame), {GN_ITERS} GN steps + fusion per frame, {FP16_WARMUP} warm-up frames, "
-                    f"{FP16_STEPS} timed",
-        "fp32": out["fp32"], "fp16": out["fp16"],
-        "max_pose_diff_fp16_vs_fp32": diff,
+        "workload": f"hashed room at 4 mm voxels (T = 2 cm), 640x480, {FP16_FRAMES} frames at 0.5 cm/frame, "
+                    f"{GN_ITERS} GN steps + fusion per frame, every frame timed, L2 flushed before each",
+        "fp32": out["fp32"], "fp16": out["fp16"], "checkpoints": checks,
         "speedup_fp16_vs_fp32": out["fp32"]["ms_per_frame"] / out["fp16"]["ms_per_frame"],
     }
 

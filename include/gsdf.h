@@ -325,19 +325,35 @@ gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, const gsdf_int
                                           double* T_wc_dev, gsdf_track_stats* stats_dev,
                                           void* cuda_stream);
 
+/* Measurement: the distinct voxels (out[0]) and distinct 8^3 blocks (out[1]; for a dense grid, the
+ * 512-voxel chunks of its linear index) that one pass over a frame touches -- the compulsory
+ * payload and table accesses of that pass, for roofline accounting (Sec. 5.3 tracks and fuses every
+ * frame; these are the voxels each of those passes must read or write at least once).
+ *   what = GSDF_FOOTPRINT_TRACK: the voxels gsdf_track_step at pose T_wc_dev reads: pixels with valid
+ *          depth whose nearest voxel (Eq. taylor) exists, is observed and has g != 0;
+ *   what = GSDF_FOOTPRINT_FUSE: the voxels gsdf_integrate of this frame at this pose updates.  Blocks
+ *          are looked up, not inserted: call it after fusing the same frame at the same pose.
+ * The map is not modified.  Synchronous; allocates and frees two bitmaps of n_voxels and n_voxels /
+ * 512 bits, so it is not meant for the per-frame loop. */
+enum { GSDF_FOOTPRINT_TRACK = 0, GSDF_FOOTPRINT_FUSE = 1 };
+gsdf_status gsdf_footprint(gsdf_handle* h, int32_t what, const float* depth_dev, const gsdf_intrinsics* K,
+                           const double* T_wc_dev, int64_t out[2]);
+
 /* ---------------------------------------------------------------------------------------------
- * Batches: many independent scenes (maps of any kind and voxel size, frames of any resolution)
- * tracked and fused together in persistent launches.  Each Gauss-Newton step of every scene is
- * one launch over (scene, pixel-tile) items pulled from a device counter.  A scene's 6x6 solve
- * runs in the block that finishes its last tile while other blocks keep working, so the
- * per-scene FP64 tail overlaps the other scenes' pixel work.  Results per scene are those of
- * gsdf_track_step / gsdf_integrate on that scene's handle, up to FP32 summation order.
+ * Batches: many independent scenes (maps of any kind, payload and voxel size, frames of any
+ * resolution) tracked and fused together in persistent launches (the tracking and fusion of
+ * Sec. 5.3, run for many scenes at once).  Each Gauss-Newton step of every scene is one launch
+ * over (scene, pixel-tile) items pulled from a device counter.  A scene's 6x6 solve runs in the
+ * block that finishes its last tile while other blocks keep working, so the per-scene FP64 tail
+ * overlaps the other scenes' pixel work.  Results per scene are those of gsdf_track_step /
+ * gsdf_integrate on that scene's handle, up to FP32 summation order.
  * ------------------------------------------------------------------------------------------- */
 typedef struct gsdf_batch gsdf_batch;
 
 /* Group n handles (all on the current device; not used elsewhere while the batch is in use).
- * Allocates the batch's descriptor table and counters.  cuda_stream: the stream of every batch
- * call.  FP16-payload handles are not accepted (GSDF_ERR_INVALID_ARG).  Synchronous. */
+ * Dense, hashed FP32 and hashed FP16 maps may be mixed.  Allocates the batch's descriptor table
+ * and counters.  cuda_stream: the stream of every batch call.  Handles with the trilinear tracker
+ * are not accepted (GSDF_ERR_INVALID_ARG).  Synchronous. */
 gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda_stream, gsdf_batch** out);
 gsdf_status gsdf_batch_destroy(gsdf_batch* b);
 
@@ -358,8 +374,26 @@ gsdf_status gsdf_batch_track_step(gsdf_batch* b);
  * gsdf_batch_set_frames).  1 <= n_iters <= 1024. */
 gsdf_status gsdf_batch_track(gsdf_batch* b, int32_t n_iters);
 
-/* Fuse every scene's frame at its current pose (prologue, one persistent launch, epilogue). */
+/* Fuse every scene's frame at its current pose (prologue, one persistent launch, for FP16 scenes
+ * one persistent apply pass, epilogue). */
 gsdf_status gsdf_batch_integrate(gsdf_batch* b);
+
+/* Per-scene depth strides for gsdf_batch_frame: stride[s] (host array of n, in floats) is added
+ * to scene s's depth pointer on the device after each frame, so that a sequence of frames stored
+ * at a fixed distance from one another (e.g. an (F, H, W) tensor: stride H*W) is walked without
+ * any call from the host.  0 keeps the pointer (the caller refills that buffer between frames,
+ * e.g. with a copy on the batch's stream).  The caller keeps every frame that will be reached
+ * valid.  Must follow gsdf_batch_set_frames; a later gsdf_batch_set_frames keeps the strides and
+ * restarts the pointers from its arguments. */
+gsdf_status gsdf_batch_set_depth_stride(gsdf_batch* b, const int64_t* stride);
+
+/* One frame of every scene (the per-frame loop of Sec. 5.3): n_iters Gauss-Newton steps
+ * (0 <= n_iters <= 1024; 0 fuses at the current poses), fusion at the tracked poses, then the depth
+ * pointers' advance (gsdf_batch_set_depth_stride).  All of it is one CUDA graph, recorded on the
+ * first call and replayed while n_iters and the tile table stay the same: one graph launch per
+ * frame, and nothing copied from the host.  Statistics: the track_stats of the last step and the
+ * frame's integrate_stats, as gsdf_batch_set_frames gave them. */
+gsdf_status gsdf_batch_frame(gsdf_batch* b, int32_t n_iters);
 
 /* Choose the tile size (pixels per work item) and the resident blocks per SM of the batched
  * tracking launch by timing candidates on the current frames: one Gauss-Newton step of every

@@ -1,16 +1,21 @@
 // Batched tracking and fusion of many independent scenes in persistent launches.
 //
-// A batch groups existing handles (dense or hashed maps of any voxel size) with one depth frame
-// per scene (any resolution).  The pixels of all scenes are cut into tiles; resident CTAs pull
-// (scene, tile) items from a device counter until none are left.
+// A batch groups existing handles (dense, hashed FP32 or hashed FP16 maps of any voxel size) with
+// one depth frame per scene (any resolution).  The pixels of all scenes are cut into tiles;
+// resident CTAs pull (scene, tile) items from a device counter until none are left.
 //   * Tracking: a tile's 30 normal-equation terms go into its scene's exact fixed-point
 //     accumulators (the same accumulators and arithmetic as the single-scene kernel), and the
 //     CTA that takes a scene's last ticket solves that scene's 6x6 system and updates its pose
 //     while the other CTAs keep working on other scenes, so the serial FP64 tail of every scene
 //     is hidden behind the others' pixel work.  One launch is one Gauss-Newton step of every
-//     scene; gsdf_batch_track records n of them into a CUDA graph that is replayed.
+//     scene.
 //   * Fusion: a prologue rounds every scene's pose once, the persistent kernel fuses all
-//     scenes' rays, an epilogue writes the per-scene block totals.
+//     scenes' rays (FP16 scenes into their frame accumulators), one persistent pass folds the
+//     FP16 scenes' accumulators into their payload, and an epilogue writes the per-scene block
+//     totals.
+//   * A frame: gsdf_batch_frame replays one CUDA graph holding n tracking launches, the fusion
+//     launches and, when strides are set, a kernel that advances every scene's depth pointer to
+//     its next frame on the device.  Nothing is uploaded from the host between frames.
 // The tile size and the number of resident CTAs per SM come from gsdf_batch_autotune, which
 // times the candidates on the batch's own frames (tracking only, on scratch copies of the poses)
 // and caches the choice per shape class (the multiset of image sizes).
@@ -26,16 +31,20 @@
 
 namespace gsdf {
 
+constexpr int kSceneDense = 0, kSceneHashed = 1, kSceneHashed16 = 2;
+
 struct SceneDesc {
-    int kind;        // GSDF_GRID_DENSE or GSDF_GRID_HASHED
+    int kind;        // kSceneDense, kSceneHashed or kSceneHashed16
     int n_px;        // pixels of the scene's frame
     int tile_begin;  // first global tile index of the scene
     int n_tiles;
     DenseMap dm;
     HashMap hm;
+    HashMap16 hm16;
     Params prm;
     Intr K;
     const float* depth;
+    long long depth_stride;  // elements the depth pointer advances after each gsdf_batch_frame
     double* pose;
     gsdf_track_stats* tstats;
     gsdf_integrate_stats* istats;
@@ -84,12 +93,16 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
         for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
         const int pix0 = p0 + threadIdx.x;
         const float d0 = pix0 < p1 ? __ldg(depth + pix0) : 0.0f;
-        if (d->kind == GSDF_GRID_DENSE) {
+        if (d->kind == kSceneDense) {
             const DenseMap m = d->dm;
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
-        } else {
+        } else if (d->kind == kSceneHashed) {
             const HashMap m = d->hm;
+            for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
+                       [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
+        } else {
+            const HashMap16 m = d->hm16;
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
         }
@@ -117,11 +130,42 @@ __global__ void batch_prologue_kernel(SceneDesc* descs, int n) {
     }
 }
 
+// Fusion epilogue: the per-scene block totals; FP16 scenes' accumulator lists are emptied (their
+// entries were folded and freed by the apply pass).
 __global__ void batch_epilogue_kernel(SceneDesc* descs, int n) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     SceneDesc* d = descs + s;
-    if (d->istats) d->istats->n_blocks_total = d->kind == GSDF_GRID_HASHED ? (long long)*d->n_blocks : 0;
+    if (d->istats) d->istats->n_blocks_total = d->kind != kSceneDense ? (long long)*d->n_blocks : 0;
+    if (d->kind == kSceneHashed16) *d->hm16.acount = 0u;
+}
+
+// FP16 scenes, second pass of fusion: every CTA walks the FP16 scenes in order and folds the
+// listed accumulator entries q = blockIdx.x, blockIdx.x + gridDim.x, ... of each.
+__global__ void __launch_bounds__(kApplyThreads)
+batch_apply16_kernel(const SceneDesc* descs, const int* __restrict__ fp16_scenes, int n_fp16) {
+    __shared__ float red[kApplyThreads / 32];
+    for (int i = 0; i < n_fp16; ++i) {
+        const SceneDesc* d = descs + __ldg(fp16_scenes + i);
+        const HashMap16 m = d->hm16;
+        const float trunc = d->prm.trunc;
+        const unsigned cnt = __ldcg(m.acount);
+        for (unsigned q = blockIdx.x; q < cnt; q += gridDim.x) apply16_entry(m, q, trunc, red);
+    }
+}
+
+// FP16 scenes, between the passes: list every FP16 scene's occupied accumulator entries (blockDim.x
+// a multiple of 32).
+__global__ void batch_list16_kernel(const SceneDesc* descs, const int* __restrict__ fp16_scenes, int n_fp16) {
+    for (int i = 0; i < n_fp16; ++i)
+        list16_entries(descs[__ldg(fp16_scenes + i)].hm16, blockIdx.x * blockDim.x + threadIdx.x,
+                       gridDim.x * blockDim.x);
+}
+
+// Advance every scene's depth pointer to its next frame (after a frame's fusion).
+__global__ void batch_advance_kernel(SceneDesc* descs, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) descs[s].depth += descs[s].depth_stride;
 }
 
 constexpr int kBatchIntThreads = 256;
@@ -151,12 +195,16 @@ batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int
         const float* depth = d->depth;
         __syncthreads();
         unsigned int rays = 0, visits = 0;
-        if (d->kind == GSDF_GRID_DENSE) {
+        if (d->kind == kSceneDense) {
             const DenseMap m = d->dm;
             for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
                 integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
-        } else {
+        } else if (d->kind == kSceneHashed) {
             const HashMap m = d->hm;
+            for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+                integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
+        } else {
+            const HashMap16 m = d->hm16;
             for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
                 integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
         }
@@ -197,8 +245,11 @@ struct gsdf_batch {
     cudaEvent_t desc_copied = nullptr;
     bool desc_pending = false;
     bool frames_set = false;
+    bool strided = false;  // some scene's depth pointer advances after each gsdf_batch_frame
     unsigned int* d_counters = nullptr;
     double* d_scratch_pose = nullptr;  // autotuning works on copies of the poses
+    int* d_fp16_scenes = nullptr;      // indices of the FP16 scenes
+    int n_fp16 = 0;
     int* d_tile_scene = nullptr;
     int tile_cap = 0;
     int total_tiles = 0;
@@ -206,9 +257,15 @@ struct gsdf_batch {
     int ctas_per_sm = 1;
     std::vector<int> n_px;  // frame size per scene in the current tile table
     std::map<std::vector<int>, std::pair<int, int>> tuned;  // shape class -> (tile_px, ctas/SM)
-    cudaGraphExec_t track_exec = nullptr;
-    int g_iters = 0, g_tiles = 0, g_tile_px = 0, g_ctas = 0;
-    const int* g_tile_ptr = nullptr;
+    // cached graphs: n tracking steps (gsdf_batch_track) and a whole frame (gsdf_batch_frame),
+    // each with the launch configuration it was recorded with
+    struct Cached {
+        cudaGraphExec_t exec = nullptr;
+        int iters = 0, tiles = 0, tile_px = 0, ctas = 0;
+        bool strided = false;
+        const int* tile_ptr = nullptr;
+    };
+    Cached track_graph, frame_graph;
 };
 
 namespace {
@@ -226,13 +283,15 @@ bool intr_ok(const gsdf_intrinsics& K) {
 }
 
 void free_batch(gsdf_batch* b) {
-    if (b->track_exec) cudaGraphExecDestroy(b->track_exec);
+    if (b->track_graph.exec) cudaGraphExecDestroy(b->track_graph.exec);
+    if (b->frame_graph.exec) cudaGraphExecDestroy(b->frame_graph.exec);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     if (b->desc_copied) cudaEventDestroy(b->desc_copied);
     cudaFree(b->d_desc);
     cudaFreeHost(b->h_desc);
     cudaFree(b->d_counters);
     cudaFree(b->d_scratch_pose);
+    cudaFree(b->d_fp16_scenes);
     cudaFree(b->d_tile_scene);
     delete b;
 }
@@ -281,10 +340,82 @@ cudaError_t launch_batch_track(gsdf_batch* b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Fusion of every scene's frame at its current pose: prologue, ray march, FP16 apply pass (if
+// the batch holds FP16 scenes), epilogue.
+cudaError_t launch_batch_fusion(gsdf_batch* b, cudaStream_t st) {
+    const int pro = (b->n + 127) / 128;
+    batch_prologue_kernel<<<pro, 128, 0, st>>>(b->d_desc, b->n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(b->total_tiles, 6 * b->num_sms));
+    batch_integrate_kernel<<<grid, kBatchIntThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles,
+                                                              b->tile_px, b->d_counters);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (b->n_fp16 > 0) {
+        batch_list16_kernel<<<2 * b->num_sms, 256, 0, st>>>(b->d_desc, b->d_fp16_scenes, b->n_fp16);
+        batch_apply16_kernel<<<16 * b->num_sms, kApplyThreads, 0, st>>>(b->d_desc, b->d_fp16_scenes, b->n_fp16);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    batch_epilogue_kernel<<<pro, 128, 0, st>>>(b->d_desc, b->n);
+    return cudaGetLastError();
+}
+
+// One frame: n_iters tracking steps, fusion, and the depth pointers' advance.
+cudaError_t launch_batch_frame(gsdf_batch* b, int n_iters, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < n_iters && e == cudaSuccess; ++it) e = launch_batch_track(b, st);
+    if (e == cudaSuccess) e = launch_batch_fusion(b, st);
+    if (e == cudaSuccess && b->strided) {
+        batch_advance_kernel<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_desc, b->n);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 std::vector<int> shape_class(const gsdf_batch* b) {
     std::vector<int> k = b->n_px;
     std::sort(k.begin(), k.end());
     return k;
+}
+
+// Replay the cached graph `g` of `record` (which launches into the stream it is given), recording
+// it again if the launch configuration changed.  When the caller's stream is itself being
+// captured, the launches go straight into the caller's graph.
+template <class F>
+cudaError_t replay(gsdf_batch* b, gsdf_batch::Cached& g, int iters, F&& record) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(b->stream, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return record(b->stream);
+    const bool same = g.exec && g.iters == iters && g.tiles == b->total_tiles && g.tile_px == b->tile_px &&
+                      g.ctas == b->ctas_per_sm && g.tile_ptr == b->d_tile_scene && g.strided == b->strided;
+    if (!same) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t le = record(b->capture_stream);
+        e = cudaStreamEndCapture(b->capture_stream, &graph);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return e;
+        }
+        g.iters = iters;
+        g.tiles = b->total_tiles;
+        g.tile_px = b->tile_px;
+        g.ctas = b->ctas_per_sm;
+        g.tile_ptr = b->d_tile_scene;
+        g.strided = b->strided;
+    }
+    return cudaGraphLaunch(g.exec, b->stream);
 }
 
 }  // namespace
@@ -295,13 +426,17 @@ gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda
     if (!out || !handles || n < 1 || n > 65536) return GSDF_ERR_INVALID_ARG;
     *out = nullptr;
     for (int s = 0; s < n; ++s)
-        if (!handles[s] || handles[s]->fp16 || handles[s]->cfg.tracker != GSDF_TRACKER_TAYLOR) return GSDF_ERR_INVALID_ARG;
+        if (!handles[s] || handles[s]->cfg.tracker != GSDF_TRACKER_TAYLOR) return GSDF_ERR_INVALID_ARG;
     gsdf_batch* b = new (std::nothrow) gsdf_batch();
     if (!b) return GSDF_ERR_OOM;
     b->n = n;
     b->stream = (cudaStream_t)cuda_stream;
     b->h.assign(handles, handles + n);
     b->n_px.assign(n, 0);
+    std::vector<int> fp16;
+    for (int s = 0; s < n; ++s)
+        if (handles[s]->fp16) fp16.push_back(s);
+    b->n_fp16 = (int)fp16.size();
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -310,6 +445,9 @@ gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * kBatchCounters);
     if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * kBatchCounters);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_scratch_pose, sizeof(double) * 16 * (size_t)n);
+    if (e == cudaSuccess && b->n_fp16 > 0) e = cudaMalloc(&b->d_fp16_scenes, sizeof(int) * fp16.size());
+    if (e == cudaSuccess && b->n_fp16 > 0)
+        e = cudaMemcpy(b->d_fp16_scenes, fp16.data(), sizeof(int) * fp16.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->desc_copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -321,9 +459,10 @@ gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda
         SceneDesc& d = b->h_desc[s];
         memset(&d, 0, sizeof(d));
         const gsdf_handle* hh = handles[s];
-        d.kind = hh->hashed ? GSDF_GRID_HASHED : GSDF_GRID_DENSE;
+        d.kind = !hh->hashed ? kSceneDense : (hh->fp16 ? kSceneHashed16 : kSceneHashed);
         d.dm = hh->dm;
         d.hm = hh->hm;
+        d.hm16 = hh->hm16;
         d.prm = hh->prm;
         d.accum = hh->sc.accum;
         d.ticket = hh->sc.counter;
@@ -383,6 +522,19 @@ gsdf_status gsdf_batch_set_frames(gsdf_batch* b, const float* const* depth_dev, 
     return batch_status(upload_desc(b));
 }
 
+gsdf_status gsdf_batch_set_depth_stride(gsdf_batch* b, const int64_t* stride) {
+    if (!b || !stride || !b->frames_set) return GSDF_ERR_INVALID_ARG;
+    cudaError_t e = wait_desc(b);
+    if (e != cudaSuccess) return batch_status(e);
+    bool any = false;
+    for (int s = 0; s < b->n; ++s) {
+        b->h_desc[s].depth_stride = (long long)stride[s];
+        any = any || stride[s] != 0;
+    }
+    b->strided = any;
+    return batch_status(upload_desc(b));
+}
+
 gsdf_status gsdf_batch_track_step(gsdf_batch* b) {
     if (!b || !b->frames_set) return GSDF_ERR_INVALID_ARG;
     return batch_status(launch_batch_track(b, b->stream));
@@ -390,55 +542,27 @@ gsdf_status gsdf_batch_track_step(gsdf_batch* b) {
 
 gsdf_status gsdf_batch_track(gsdf_batch* b, int32_t n_iters) {
     if (!b || !b->frames_set || n_iters < 1 || n_iters > 1024) return GSDF_ERR_INVALID_ARG;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaError_t e = cudaStreamIsCapturing(b->stream, &cs);
-    if (e != cudaSuccess) return batch_status(e);
-    if (cs != cudaStreamCaptureStatusNone) {
-        for (int it = 0; it < n_iters && e == cudaSuccess; ++it) e = launch_batch_track(b, b->stream);
-        return batch_status(e);
-    }
-    const bool same = b->track_exec && b->g_iters == n_iters && b->g_tiles == b->total_tiles &&
-                      b->g_tile_px == b->tile_px && b->g_ctas == b->ctas_per_sm && b->g_tile_ptr == b->d_tile_scene;
-    if (!same) {
-        if (b->track_exec) {
-            cudaGraphExecDestroy(b->track_exec);
-            b->track_exec = nullptr;
-        }
-        cudaGraph_t graph = nullptr;
-        e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return batch_status(e);
-        cudaError_t le = cudaSuccess;
-        for (int it = 0; it < n_iters && le == cudaSuccess; ++it) le = launch_batch_track(b, b->capture_stream);
-        e = cudaStreamEndCapture(b->capture_stream, &graph);
-        if (le != cudaSuccess) e = le;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->track_exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            b->track_exec = nullptr;
-            return batch_status(e);
-        }
-        b->g_iters = n_iters;
-        b->g_tiles = b->total_tiles;
-        b->g_tile_px = b->tile_px;
-        b->g_ctas = b->ctas_per_sm;
-        b->g_tile_ptr = b->d_tile_scene;
-    }
-    return batch_status(cudaGraphLaunch(b->track_exec, b->stream));
+    return batch_status(replay(b, b->track_graph, n_iters, [&](cudaStream_t st) {
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < n_iters && e == cudaSuccess; ++it) e = launch_batch_track(b, st);
+        return e;
+    }));
 }
 
 gsdf_status gsdf_batch_integrate(gsdf_batch* b) {
     if (!b || !b->frames_set) return GSDF_ERR_INVALID_ARG;
-    const int pro = (b->n + 127) / 128;
-    batch_prologue_kernel<<<pro, 128, 0, b->stream>>>(b->d_desc, b->n);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return batch_status(e);
-    const int grid = std::max(1, std::min(b->total_tiles, 6 * b->num_sms));
-    batch_integrate_kernel<<<grid, kBatchIntThreads, 0, b->stream>>>(b->d_desc, b->d_tile_scene, b->total_tiles,
-                                                                     b->tile_px, b->d_counters);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return batch_status(e);
-    batch_epilogue_kernel<<<pro, 128, 0, b->stream>>>(b->d_desc, b->n);
-    return batch_status(cudaGetLastError());
+    return batch_status(launch_batch_fusion(b, b->stream));
+}
+
+gsdf_status gsdf_batch_frame(gsdf_batch* b, int32_t n_iters) {
+    if (!b || !b->frames_set || n_iters < 0 || n_iters > 1024) return GSDF_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (b->strided) e = wait_desc(b);  // the host copy of the pointers is advanced below
+    if (e == cudaSuccess)
+        e = replay(b, b->frame_graph, n_iters, [&](cudaStream_t st) { return launch_batch_frame(b, n_iters, st); });
+    if (e == cudaSuccess && b->strided)  // keep the host copy of the table in step with the device's
+        for (int s = 0; s < b->n; ++s) b->h_desc[s].depth += b->h_desc[s].depth_stride;
+    return batch_status(e);
 }
 
 gsdf_status gsdf_batch_autotune(gsdf_batch* b, int32_t* tile_px_out, int32_t* ctas_per_sm_out) {

@@ -158,7 +158,7 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
         if (e == cudaSuccess) e = cudaMalloc(&m.W, sizeof(float) * (size_t)h->n_voxels);
         if (e == cudaSuccess) e = cudaMalloc(&m.scale, sizeof(float) * slots);
         if (e == cudaSuccess) e = cudaMalloc(&m.akeys, sizeof(int) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&m.alist, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&m.alist, sizeof(int2) * cap);
         if (e == cudaSuccess) e = cudaMalloc(&m.acount, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemsetAsync(m.acount, 0, sizeof(unsigned int), h->stream);
         if (e == cudaSuccess) e = cudaMalloc(&m.accA, sizeof(float4) * cap * kBlockVoxels);

@@ -181,8 +181,9 @@ struct HashMap {
 // gbar = g / W (|gbar| <= 1, same direction as g), and W in FP32; per block: sigma_b, a scale that
 // only grows (the largest |psi| the block has held).  A frame is fused in two passes: the ray march
 // adds (w d, w n, w) into FP32 accumulators of the blocks it touches, kept in a small
-// open-addressing table keyed by hash slot, then one CTA per occupied accumulator entry folds them
-// in with Eq. (sdf_update) / (gradient_update) and re-encodes (round to nearest).
+// open-addressing table keyed by hash slot; the occupied entries are listed, then one CTA per
+// listed entry folds them in with Eq. (sdf_update) / (gradient_update) and re-encodes (round to
+// nearest).
 struct HashMap16 {
     HashMap base;      // keys, mask, probe limit (its A and W are unused)
     ushort4* H;        // [slots * 512] half bits of (psi / sigma_b, gbar_x, gbar_y, gbar_z)
@@ -192,8 +193,8 @@ struct HashMap16 {
     unsigned int amask;  // acap - 1 (acap a power of two)
     float4* accA;      // [acap * 512] (sum w d, sum w n)
     float* accW;       // [acap * 512] sum w
-    int* alist;        // [acap] occupied entries, listed by the apply pass
-    unsigned int* acount;
+    int* alist;        // [2 acap] (entry, hash slot) of the occupied entries, listed after the march
+    unsigned int* acount;  // number of listed entries (cleared once the apply pass is done)
 
     __device__ __forceinline__ long long find(int mx, int my, int mz) const { return base.find(mx, my, mz); }
     __device__ __forceinline__ bool voxel(long long idx, float& psi, float& gx, float& gy, float& gz) const {

@@ -53,94 +53,17 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
     }
 }
 
-// FP16 maps, second pass.  The occupied accumulator entries are listed first; then one block per
-// listed entry folds the frame's sums into the voxels that received updates, with Eqs.
-// (sdf_update) and (gradient_update) in FP32:
-//   W' = W + S_w,  psi' = (W psi + S_d) / W',  gbar' = (W gbar + S_n) / W',
-// and re-encodes them (psi' / sigma_b, gbar') to FP16 with round-to-nearest.  The block scale
-// becomes max(sigma_b, max |psi'| over the updated voxels); the other voxels already satisfy
-// |psi| <= sigma_b, so only when the scale grows are they re-encoded too.  The entry's
-// accumulators are cleared and the entry freed for the next frame.
+// FP16 maps: the frame's occupied accumulator entries (list16_entries).  blockDim.x is a
+// multiple of 32.
 __global__ void list16_kernel(HashMap16 m) {
-    const unsigned n = m.amask + 1u;
-    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        if (m.akeys[e] >= 0) m.alist[atomicAdd(m.acount, 1u)] = (int)e;
+    list16_entries(m, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-constexpr int kApplyThreads = 256;
-constexpr int kApplyPer = kBlockVoxels / kApplyThreads;
-
+// FP16 maps, second pass: one block per listed accumulator entry (apply16_entry).
 __global__ void __launch_bounds__(kApplyThreads) apply16_kernel(HashMap16 m, float trunc) {
     __shared__ float red[kApplyThreads / 32];
-    const unsigned cnt = *m.acount;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (unsigned q = blockIdx.x; q < cnt; q += gridDim.x) {
-        const unsigned ci = (unsigned)m.alist[q];
-        const int slot = m.akeys[ci];
-        const float sigma = m.scale[slot];
-        const long long gbase = (long long)slot * kBlockVoxels, abase = (long long)ci * kBlockVoxels;
-        float psi[kApplyPer], g0[kApplyPer], g1[kApplyPer], g2[kApplyPer], w[kApplyPer], sw[kApplyPer];
-        float4 sa[kApplyPer];
-        ushort4 h[kApplyPer];
-#pragma unroll
-        for (int k = 0; k < kApplyPer; ++k) {
-            const int v = threadIdx.x + k * kApplyThreads;
-            sw[k] = m.accW[abase + v];
-            sa[k] = m.accA[abase + v];
-            h[k] = m.H[gbase + v];
-            w[k] = m.W[gbase + v];
-        }
-        float amax = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kApplyPer; ++k) {
-            psi[k] = __half2float(__ushort_as_half(h[k].x)) * sigma;
-            g0[k] = __half2float(__ushort_as_half(h[k].y));
-            g1[k] = __half2float(__ushort_as_half(h[k].z));
-            g2[k] = __half2float(__ushort_as_half(h[k].w));
-            if (sw[k] > 0.0f) {
-                const float wn = w[k] + sw[k];
-                psi[k] = (w[k] * psi[k] + sa[k].x) / wn;
-                g0[k] = (w[k] * g0[k] + sa[k].y) / wn;
-                g1[k] = (w[k] * g1[k] + sa[k].z) / wn;
-                g2[k] = (w[k] * g2[k] + sa[k].w) / wn;
-                w[k] = wn;
-                amax = fmaxf(amax, fabsf(psi[k]));
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        if (lane == 0) red[warp] = amax;
-        __syncthreads();
-        float bmax = red[0];
-#pragma unroll
-        for (int k = 1; k < kApplyThreads / 32; ++k) bmax = fmaxf(bmax, red[k]);
-        float sig = fmaxf(sigma, bmax);
-        if (!(sig > 0.0f)) sig = trunc;  // nothing observed yet: any positive scale encodes zeros
-        const bool rescale = sig != sigma && sigma > 0.0f;
-#pragma unroll
-        for (int k = 0; k < kApplyPer; ++k) {
-            const int v = threadIdx.x + k * kApplyThreads;
-            if (sw[k] > 0.0f) {
-                ushort4 o4;
-                o4.x = __half_as_ushort(__float2half_rn(psi[k] / sig));
-                o4.y = __half_as_ushort(__float2half_rn(g0[k]));
-                o4.z = __half_as_ushort(__float2half_rn(g1[k]));
-                o4.w = __half_as_ushort(__float2half_rn(g2[k]));
-                m.H[gbase + v] = o4;
-                m.W[gbase + v] = w[k];
-                m.accA[abase + v] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                m.accW[abase + v] = 0.0f;
-            } else if (rescale) {
-                ushort4 hh = h[k];
-                hh.x = __half_as_ushort(__float2half_rn(psi[k] / sig));
-                m.H[gbase + v] = hh;
-            }
-        }
-        if (threadIdx.x == 0) {
-            m.scale[slot] = sig;
-            m.akeys[ci] = -1;
-        }
-        __syncthreads();
-    }
+    const unsigned cnt = __ldcg(m.acount);
+    for (unsigned q = blockIdx.x; q < cnt; q += gridDim.x) apply16_entry(m, q, trunc, red);
 }
 
 __global__ void integrate_stats_total(gsdf_integrate_stats* stats, const unsigned int* n_blocks) {

@@ -165,6 +165,106 @@ __device__ __forceinline__ long long voxel_index<DenseMap>(const DenseMap& map, 
     return map.find(mx, my, mz);
 }
 
+// FP16 maps, second pass: fold listed accumulator entry q (of *m.acount) into its block, with
+// Eqs. (sdf_update) and (gradient_update) in FP32 for the voxels that received updates:
+//   W' = W + S_w,  psi' = (W psi + S_d) / W',  gbar' = (W gbar + S_n) / W',
+// re-encoded (psi' / sigma_b, gbar') to FP16 with round-to-nearest.  The block scale becomes
+// max(sigma_b, max |psi'| over the updated voxels); the other voxels already satisfy
+// |psi| <= sigma_b, so only when the scale grows are they re-encoded too.  kApplyThreads threads
+// fold one entry, thread t taking voxels t + kApplyThreads k: every thread first reads its
+// voxels' weight sums, then issues the payload and sum loads of all its updated voxels together;
+// a voxel without updates costs that one 4-byte read (its payload is read only when the scale
+// grows).  The entry's sums are cleared and the entry freed for the next frame.  Called by all
+// threads of the block, uniformly; red: kApplyThreads / 32 floats of shared memory.
+constexpr int kApplyThreads = 128;
+constexpr int kApplyPer = kBlockVoxels / kApplyThreads;
+
+// FP16 maps, between the passes: list the occupied accumulator entries of the frame as (entry,
+// hash slot) pairs, with one atomic per warp that finds any.  Entries e = first, first + stride,
+// ...; called by whole warps (the loop runs to the table size rounded up to 32).
+__device__ __forceinline__ void list16_entries(const HashMap16& m, unsigned first, unsigned stride) {
+    const unsigned n = m.amask + 1u;
+    const unsigned nr = (n + 31u) & ~31u;
+    const int lane = threadIdx.x & 31;
+    for (unsigned e = first; e < nr; e += stride) {
+        const int slot = e < n ? __ldcg(m.akeys + e) : -1;
+        const unsigned b = __ballot_sync(0xffffffffu, slot >= 0);
+        unsigned base = 0u;
+        if (lane == 0 && b) base = atomicAdd(m.acount, (unsigned)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (slot >= 0)
+            reinterpret_cast<int2*>(m.alist)[base + __popc(b & ((1u << lane) - 1u))] = make_int2((int)e, slot);
+    }
+}
+
+__device__ __forceinline__ void apply16_entry(const HashMap16& m, unsigned q, float trunc, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int2 e = __ldcg(reinterpret_cast<const int2*>(m.alist) + q);  // (entry, hash slot)
+    const unsigned ci = (unsigned)e.x;
+    const int slot = e.y;
+    const float sigma = __ldcg(m.scale + slot);
+    const long long gbase = (long long)slot * kBlockVoxels, abase = (long long)ci * kBlockVoxels;
+    float sw[kApplyPer];
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k) sw[k] = __ldcg(m.accW + abase + threadIdx.x + k * kApplyThreads);
+    float4 sa[kApplyPer];
+    ushort4 h[kApplyPer];
+    float w[kApplyPer];
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k) {
+        const int v = threadIdx.x + k * kApplyThreads;
+        const bool upd = sw[k] > 0.0f;
+        sa[k] = upd ? __ldcg(m.accA + abase + v) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        h[k] = upd ? __ldcg(m.H + gbase + v) : make_ushort4(0, 0, 0, 0);
+        w[k] = upd ? __ldcg(m.W + gbase + v) : 0.0f;
+    }
+    float psi[kApplyPer], g0[kApplyPer], g1[kApplyPer], g2[kApplyPer];
+    float amax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k) {
+        const float wn = w[k] + sw[k];
+        psi[k] = (w[k] * (__half2float(__ushort_as_half(h[k].x)) * sigma) + sa[k].x) / wn;
+        g0[k] = (w[k] * __half2float(__ushort_as_half(h[k].y)) + sa[k].y) / wn;
+        g1[k] = (w[k] * __half2float(__ushort_as_half(h[k].z)) + sa[k].z) / wn;
+        g2[k] = (w[k] * __half2float(__ushort_as_half(h[k].w)) + sa[k].w) / wn;
+        w[k] = wn;
+        if (sw[k] > 0.0f) amax = fmaxf(amax, fabsf(psi[k]));
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) red[warp] = amax;
+    __syncthreads();
+    float bmax = red[0];
+#pragma unroll
+    for (int k = 1; k < kApplyThreads / 32; ++k) bmax = fmaxf(bmax, red[k]);
+    float sig = fmaxf(sigma, bmax);
+    if (!(sig > 0.0f)) sig = trunc;  // nothing observed yet: any positive scale encodes zeros
+    const bool rescale = sig != sigma && sigma > 0.0f;
+#pragma unroll
+    for (int k = 0; k < kApplyPer; ++k) {
+        const int v = threadIdx.x + k * kApplyThreads;
+        if (sw[k] > 0.0f) {
+            ushort4 o4;
+            o4.x = __half_as_ushort(__float2half_rn(psi[k] / sig));
+            o4.y = __half_as_ushort(__float2half_rn(g0[k]));
+            o4.z = __half_as_ushort(__float2half_rn(g1[k]));
+            o4.w = __half_as_ushort(__float2half_rn(g2[k]));
+            m.H[gbase + v] = o4;
+            m.W[gbase + v] = w[k];
+            m.accA[abase + v] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            m.accW[abase + v] = 0.0f;
+        } else if (rescale) {
+            ushort4 hh = __ldcg(m.H + gbase + v);
+            hh.x = __half_as_ushort(__float2half_rn((__half2float(__ushort_as_half(hh.x)) * sigma) / sig));
+            m.H[gbase + v] = hh;
+        }
+    }
+    if (threadIdx.x == 0) {
+        m.scale[slot] = sig;
+        m.akeys[ci] = -1;
+    }
+    __syncthreads();
+}
+
 // Fuse the ray of pixel `pix` (Eqs. (sdf_update), (gradient_update), Sec. 5.3) into the map:
 // validity and normal test, then every distinct voxel of the ray's samples inside the band
 // receives (w d, w n_w) and w.  `pose` is the FP32-rounded pose; counts go to rays / visits.

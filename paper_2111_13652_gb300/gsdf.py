@@ -29,6 +29,8 @@ GSDF_PAYLOAD_F32 = 0
 GSDF_PAYLOAD_F16 = 1
 GSDF_TRACKER_TAYLOR = 0
 GSDF_TRACKER_TRILINEAR = 1
+GSDF_FOOTPRINT_TRACK = 0
+GSDF_FOOTPRINT_FUSE = 1
 GSDF_BA_POSES = 1
 GSDF_BA_PSI = 2
 
@@ -104,6 +106,9 @@ _SIGS = {
     "gsdf_batch_track": (C.c_int, [C.c_void_p, C.c_int32]),
     "gsdf_batch_integrate": (C.c_int, [C.c_void_p]),
     "gsdf_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int32), _P(C.c_int32)]),
+    "gsdf_batch_set_depth_stride": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
+    "gsdf_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, _P(C.c_int64)]),
+    "gsdf_batch_frame": (C.c_int, [C.c_void_p, C.c_int32]),
     "gsdf_track_step_dense_noalloc": (C.c_int, [C.c_void_p, _P(gsdf_intrinsics), C.c_void_p, C.c_void_p,
                                                 _P(C.c_int32), _P(C.c_int32), C.c_float, C.c_float, C.c_double,
                                                 C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -447,6 +452,14 @@ class Map:
         _check(st, "gsdf_extract_mesh")
         return out[:n]
 
+    def footprint(self, what: int, depth, K: gsdf_intrinsics, pose):
+        """(distinct voxels, distinct blocks) one tracking step (GSDF_FOOTPRINT_TRACK) or one fusion
+        (GSDF_FOOTPRINT_FUSE, after fusing that frame at that pose) touches (gsdf_footprint)."""
+        out = (C.c_int64 * 2)()
+        _check(load_library().gsdf_footprint(C.c_void_p(self.h), what, C.c_void_p(depth.data_ptr()), C.byref(K),
+                                              C.c_void_p(pose.data_ptr()), out), "gsdf_footprint")
+        return int(out[0]), int(out[1])
+
     def load(self, vox: np.ndarray):
         _check(gsdf_load_voxels(self.h, vox), "gsdf_load_voxels")
 
@@ -495,6 +508,15 @@ class Batch:
 
     def integrate(self):
         _check(load_library().gsdf_batch_integrate(C.c_void_p(self.b)), "gsdf_batch_integrate")
+
+    def set_depth_stride(self, strides):
+        """Per-scene depth strides in floats (gsdf_batch_set_depth_stride)."""
+        arr = (C.c_int64 * len(self.maps))(*[int(x) for x in strides])
+        _check(load_library().gsdf_batch_set_depth_stride(C.c_void_p(self.b), arr), "gsdf_batch_set_depth_stride")
+
+    def frame(self, n_iters: int):
+        """One frame of every scene: n_iters Gauss-Newton steps, fusion, depth advance (one graph)."""
+        _check(load_library().gsdf_batch_frame(C.c_void_p(self.b), n_iters), "gsdf_batch_frame")
 
     def autotune(self):
         t, c = C.c_int32(), C.c_int32()

@@ -416,14 +416,24 @@ class RoomSequence:
 
 
 def room_sequence(seed: int = 2, n_frames: int = 100, cam: Camera = KINECT_640, voxel_size=0.01,
-                  noise=True, frames_per_segment=25) -> RoomSequence:
-    """Room scene, smooth trajectory and noisy depth frames (sigma = 0.0012 z^2)."""
+                  noise=True, frames_per_segment=25, processes: int = 1) -> RoomSequence:
+    """Room scene, smooth trajectory and noisy depth frames (sigma = 0.0012 z^2).  `processes` > 1
+    ray-casts the frames in a spawned pool; the noise is drawn afterwards in frame order, so the
+    frames do not depend on it."""
     scene = make_room(seed)
     poses = room_trajectory(scene, n_frames, seed, frames_per_segment)
     rng = np.random.default_rng(seed + 104729)
+    if processes > 1:
+        import concurrent.futures as cf
+        import functools
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+            clean = list(ex.map(functools.partial(render_depth, scene, cam), poses, chunksize=4))
+    else:
+        clean = [render_depth(scene, cam, T) for T in poses]
     depths = np.empty((n_frames, cam.height, cam.width), np.float32)
-    for f, T in enumerate(poses):
-        d = render_depth(scene, cam, T)
+    for f, d in enumerate(clean):
         depths[f] = add_depth_noise(d, rng) if noise else d
     return RoomSequence(cam, scene, poses, depths, voxel_size, 5 * voxel_size)
 

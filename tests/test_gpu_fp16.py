@@ -106,5 +106,52 @@ def test_fp16_checkpoint_roundtrip_and_capacity(G, room4mm):
     small.integrate(_dev(s.depths[0]), K, _dev(s.poses[0]))
     assert G.gsdf_sync(small.h) == G.GSDF_ERR_CAPACITY
     assert 0 < small.num_blocks()
+    tri = G.Map(G.make_config(s.voxel_size, hash_slots=1 << 10, tracker=G.GSDF_TRACKER_TRILINEAR))
     with pytest.raises(G.GsdfError):
-        G.Batch([m])  # FP16 handles are not batched
+        G.Batch([m, tri])  # the trilinear tracker is not batched
+
+
+def test_fp16_in_a_batch_matches_oracle(G, room4mm):
+    """An FP16 scene and an FP32 scene of the 4 mm room in one batch: three frames through
+    gsdf_batch_frame (frame 0 fused at its true pose, frames 1 and 2 each fused after 10 batched
+    Gauss-Newton steps), the depth pointers advanced on the device.  Each scene against the FP64
+    oracle run in lockstep (the oracle
+    starts every tracking run from the batch's pose and fuses at the batch's tracked pose): voxel
+    set exact, psi within 2 * 2^-11 T (FP16) or 1e-5 (FP32), ghat within 1e-3 (FP16) or 1e-5,
+    poses within 1e-4."""
+    s = room4mm
+    T = 5 * s.voxel_size
+    maps = [_fp16_map(G, s.voxel_size), G.Map(G.make_config(s.voxel_size, hash_slots=1 << 17))]
+    batch = G.Batch(maps)
+    K = G.intrinsics(s.cam)
+    depths = _dev(s.depths)
+    poses = [_dev(s.poses[0]) for _ in maps]
+    batch.set_frames([depths[0], depths[0]], [K, K], poses)
+    batch.set_depth_stride([s.cam.width * s.cam.height] * 2)
+    oms = [O.OracleMap(O.params(s.voxel_size)) for _ in maps]
+    Tprev = [s.poses[0]] * 2
+    for f in range(3):
+        batch.frame(0 if f == 0 else 10)  # tracks frame f (f > 0), fuses it, advances to f + 1
+        torch.cuda.synchronize()
+        for k, om in enumerate(oms):
+            Tg = poses[k].cpu().numpy()
+            if f > 0:
+                To = Tprev[k].copy()
+                for _ in range(10):
+                    To, _ = om.track_step(s.depths[f], s.cam, To)
+                diff = np.abs(Tg - To).max()
+                print(f"batched {'fp16' if k == 0 else 'fp32'} frame {f}: pose difference {diff:.3e}")
+                assert diff < 1e-4, (k, f, diff)
+            om.integrate(s.depths[f], s.cam, Tg)
+            Tprev[k] = Tg
+    for k, (m, om) in enumerate(zip(maps, oms)):
+        m.sync()
+        gv, ov = _sorted(m.extract()), om.extract()
+        assert np.array_equal(gv["m"], ov["m"]), k
+        dpsi = np.abs(gv["psi"] - ov["psi"]).max()
+        dg = np.abs(_ghat(gv["g"].astype(np.float64)) - _ghat(ov["g"])).max()
+        print(f"batched {'fp16' if k == 0 else 'fp32'}: max |dpsi| {dpsi:.3e}, max |dghat| {dg:.3e}")
+        assert dpsi <= (2 * 2**-11 * T + 1e-6 if k == 0 else 1e-5)
+        assert dg <= (1e-3 if k == 0 else 1e-5)
+        assert np.max(np.abs(gv["w"] - ov["w"]) / ov["w"]) <= 1e-5
+    batch.close()
