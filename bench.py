@@ -247,7 +247,9 @@ def run_oracle_replicas(seq, first, count, n):
 
     ctx = mp.get_context("spawn")
     k = first + count
-    with ctx.Manager() as mgr:
+    from paper_2111_13652_gb300 import inputs as I
+
+    with I._SingleThreadedChildren(), ctx.Manager() as mgr:
         bar = mgr.Barrier(n)
         job = (seq.depths[:k], seq.cam, [np.asarray(T) for T in seq.poses[:k]], first, count, bar)
         with cf.ProcessPoolExecutor(n, mp_context=ctx) as ex:
@@ -338,7 +340,7 @@ def gpu_arm(args):
 
         # the 4 mm room: 300 frames at 0.5 cm per frame
         fp16_seq = I.room_sequence(seed=SEED, n_frames=1 + FP16_FRAMES, voxel_size=FP16_VOXEL,
-                                   frames_per_segment=75, processes=procs)
+                                   frames_per_segment=75, processes=procs, conditioned_horizon=1 + FP16_FRAMES)
     keyframes = None
     if not args.no_adjoint_form:
         from paper_2111_13652_gb300 import inputs as I
@@ -828,21 +830,20 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
         m.close()
 
     def field_diff(a, b):
-        ka = {tuple(x): i for i, x in enumerate(a["m"])}
-        ib, ia = [], []
-        for j, x in enumerate(b["m"]):
-            i = ka.get(tuple(x))
-            if i is not None:
-                ia.append(i)
-                ib.append(j)
-        ga = a["g"][ia].astype(np.float64)
-        gb = b["g"][ib].astype(np.float64)
+        """FP16 against FP32 fields on their common voxels.  The two runs track independently, so
+        their poses differ slightly and a voxel at the band edge can take one more or one fewer ray
+        in one of them; such voxels set the maximum, the percentiles show the bulk (the FP16 payload
+        against the FP64 oracle at identical poses is bounded in the GPU tests)."""
+        key = lambda m: ((m[:, 0].astype(np.int64) + (1 << 20)) << 42) | ((m[:, 1].astype(np.int64) + (1 << 20)) << 21) \
+            | (m[:, 2].astype(np.int64) + (1 << 20))  # noqa: E731
+        _, ia, ib = np.intersect1d(key(a["m"]), key(b["m"]), assume_unique=True, return_indices=True)
         gh = lambda g: g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-30)  # noqa: E731
         dpsi = np.abs(a["psi"][ia].astype(np.float64) - b["psi"][ib])
-        dg = np.abs(gh(ga) - gh(gb)).max(axis=1)
+        dg = np.abs(gh(a["g"][ia].astype(np.float64)) - gh(b["g"][ib].astype(np.float64))).max(axis=1)
+        pct = lambda x: {p: float(np.percentile(x, q)) for p, q in (("p50", 50), ("p99", 99), ("p999", 99.9))}  # noqa: E731
         return {"common_voxels": len(ia), "only_fp32": len(a) - len(ia), "only_fp16": len(b) - len(ib),
-                "max_dpsi": float(dpsi.max()), "mean_dpsi": float(dpsi.mean()),
-                "max_dghat": float(dg.max()), "mean_dghat": float(dg.mean())}
+                "max_dpsi": float(dpsi.max()), "mean_dpsi": float(dpsi.mean()), "dpsi": pct(dpsi),
+                "max_dghat": float(dg.max()), "mean_dghat": float(dg.mean()), "dghat": pct(dg)}
 
     checks = {}
     for c in FP16_CHECKS:

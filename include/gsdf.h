@@ -310,11 +310,13 @@ gsdf_status gsdf_sync(gsdf_handle* h);
  *   cuda_stream the stream to launch on (NULL = legacy default stream).
  * Scratch: a 16,640-byte array in the library's device memory (a static __device__ array that
  * every GPU which loads the library holds until the process exits).  The scratch this step
- * needs does not grow with the image or grid size; a request needing more than the array holds
- * would return GSDF_ERR_CAPACITY.  Inputs beyond the limits gsdf_create and gsdf_track_step
- * accept (image sides > 32768, grid sides > 65536) return GSDF_ERR_INVALID_ARG.
+ * needs does not grow with the image or grid size: its fit is fixed when the library is built,
+ * so this call never reports GSDF_ERR_CAPACITY.  Inputs beyond the limits gsdf_create and
+ * gsdf_track_step accept (image sides > 32768, grid sides > 65536) return GSDF_ERR_INVALID_ARG.
  * The first call on a device resolves the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call clears the
+ * that device current and keeps it for the life of the process; make that first call before any
+ * stream capture.  A reset of the device's context (cudaDeviceReset) invalidates the kept address:
+ * after one, restart the process before calling this entry point again.  Every call clears the
  * array's accumulators on cuda_stream before using them, and all calls share the one array:
  * calls that may overlap on the GPU (different streams, or the same call issued into several
  * concurrently running graphs) race with each other and must be serialised by the caller. */

@@ -127,17 +127,8 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
         return GSDF_ERR_CUDA;
     }
     h->hashed = cfg->grid_kind == GSDF_GRID_HASHED;
-    Params& p = h->prm;
-    p.vs = cfg->voxel_size;
-    p.inv_vs = (float)(1.0 / (double)cfg->voxel_size);
-    p.trunc = cfg->truncation;
-    p.eps = cfg->weight_eps;
-    p.half_vs = 0.5f * cfg->voxel_size;
-    p.huber = cfg->huber_delta;
-    p.cos_max = cfg->cos_max_angle;
-    p.band_half = (int)ceil((double)cfg->truncation / (double)p.half_vs - 1e-6);
-    p.damping = cfg->damping;
-    p.lam_scale = cfg->damping / 6.0;
+    h->prm = make_params(cfg->voxel_size, cfg->truncation, cfg->weight_eps, cfg->huber_delta, cfg->cos_max_angle,
+                         cfg->damping);
 
     cudaError_t e = cudaSuccess;
     float4* A = nullptr;

@@ -10,6 +10,8 @@
 //   psi = A.x / W when read.
 #pragma once
 
+#include <math.h>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -38,6 +40,24 @@ struct Params {
     double damping;
     double lam_scale;  // damping / 6: the Levenberg term is lam_scale * trace(H)
 };
+
+// The method parameters as the kernels use them, from the configuration values (the one place
+// both gsdf_create and the allocation-free tracking step build them).
+inline Params make_params(float voxel_size, float truncation, float weight_eps, float huber_delta,
+                          float cos_max_angle, double damping) {
+    Params p;
+    p.vs = voxel_size;
+    p.inv_vs = (float)(1.0 / (double)voxel_size);
+    p.trunc = truncation;
+    p.eps = weight_eps;
+    p.half_vs = 0.5f * voxel_size;
+    p.huber = huber_delta;
+    p.cos_max = cos_max_angle;
+    p.band_half = (int)ceil((double)truncation / (double)p.half_vs - 1e-6);
+    p.damping = damping;
+    p.lam_scale = damping / 6.0;
+    return p;
+}
 
 // Pose rounded once from FP64: camera->world (R, t) and world->camera (R^T, -R^T t).
 struct PoseF {

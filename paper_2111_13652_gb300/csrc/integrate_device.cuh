@@ -38,19 +38,39 @@ __device__ __forceinline__ bool pixel_normal(const float* __restrict__ depth, co
     n[2] = __fsub_rn(__fmul_rn(a[0], b[1]), __fmul_rn(a[1], b[0]));
     const float nn = dot3_rn(n, n);
     if (!(nn > 0.0f)) return false;
-    const float s = __fsqrt_rn(nn);
-    n[0] = __fdiv_rn(n[0], s);
-    n[1] = __fdiv_rn(n[1], s);
-    n[2] = __fdiv_rn(n[2], s);
-    float dp = dot3_rn(n, p);
-    if (dp < 0.0f) {
-        n[0] = -n[0];
-        n[1] = -n[1];
-        n[2] = -n[2];
-        dp = -dp;
+    // The 75 degree test is a discrete decision and is taken exactly as specified: n normalised by
+    // correctly rounded divisions, oriented so that n . p > 0, and c = (n . p) / sqrt(p . p)
+    // compared with cos_max.  Most pixels are decided by a cheap evaluation of the same cosine,
+    // |n . p| rsqrt(n . n) rsqrt(p . p): both evaluations are within 3e-6 (relative) of the true
+    // cosine near the threshold (a dozen roundings of at most 2^-24, reciprocal square roots within
+    // 2 ulp, cancellation in n . p at most 1 / c <= 4), so outside a margin of 4e-5 cos_max they take
+    // the same decision; inside it the exact evaluation decides.  The normal returned feeds sums
+    // only (Eq. gradient_update), so it is scaled by the reciprocal square root.
+    const float pp = dot3_rn(p, p);
+    const float dpr = dot3_rn(n, p);
+    const float rn = rsqrtf(nn);
+    const float cf = fabsf(dpr) * rn * rsqrtf(pp);
+    const float margin = 4e-5f * fabsf(prm.cos_max) + 1e-7f;
+    const bool fast = nn > 1e-30f && pp > 1e-30f && fabsf(cf - prm.cos_max) > margin;
+    bool keep = cf > prm.cos_max;
+    // the sign of the raw n . p orients the normal whenever |n . p| is clearly above rounding
+    // (cf > 1e-4); a kept normal nearly perpendicular to its ray (possible only for cos_max < 1e-4)
+    // takes the orientation of the exact evaluation too
+    bool neg = dpr < 0.0f;
+    if (!fast || (keep && !(cf > 1e-4f))) {
+        const float s = __fsqrt_rn(nn);
+        const float e[3] = {__fdiv_rn(n[0], s), __fdiv_rn(n[1], s), __fdiv_rn(n[2], s)};
+        float dp = dot3_rn(e, p);
+        neg = dp < 0.0f;
+        if (neg) dp = -dp;
+        keep = __fdiv_rn(dp, __fsqrt_rn(pp)) >= prm.cos_max;
     }
-    const float c = __fdiv_rn(dp, __fsqrt_rn(dot3_rn(p, p)));
-    return c >= prm.cos_max;
+    if (!keep) return false;
+    const float k = neg ? -rn : rn;
+    n[0] *= k;
+    n[1] *= k;
+    n[2] *= k;
+    return true;
 }
 
 // Per-ray cache of the last block looked up (consecutive voxels of a ray mostly share a block),

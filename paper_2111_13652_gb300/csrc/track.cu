@@ -93,7 +93,9 @@ cudaError_t launch_track_trilinear(const DenseMap* dm, const HashMap* hm, const 
 namespace gsdf {
 namespace {
 
-// kAccumWords accumulator words, then one word for the ticket counter, padded: 16640 bytes.
+// kAccumWords accumulator words, then one word for the ticket counter, padded: 16640 bytes.  The
+// scratch a tracking step needs does not depend on the image or grid size (the accumulators are
+// replicated a fixed number of times), so its fit is checked here, at compile time.
 constexpr size_t kStaticScratchWords = kAccumWords + 32;
 constexpr size_t kStaticScratchNeeded = kAccumWords + 1;
 static_assert(kStaticScratchNeeded <= kStaticScratchWords, "static scratch too small");
@@ -129,9 +131,6 @@ extern "C" gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, con
         if ((long long)origin[i] < -(1ll << 23) || (long long)origin[i] + dims[i] > (1ll << 23)) return GSDF_ERR_INVALID_ARG;
     }
     if (n > (1ll << 34)) return GSDF_ERR_INVALID_ARG;
-    // the scratch this call needs must fit the static array (it does not depend on the input
-    // sizes: the accumulators are replicated a fixed number of times)
-    if (kStaticScratchNeeded > kStaticScratchWords) return GSDF_ERR_CAPACITY;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GSDF_ERR_CUDA;
@@ -173,12 +172,9 @@ extern "C" gsdf_status gsdf_track_step_dense_noalloc(const float* depth_dev, con
     ki.depth_max = K->depth_max;
     ki.ifx = (float)(1.0 / (double)K->fx);
     ki.ify = (float)(1.0 / (double)K->fy);
-    Params prm = {};
-    prm.vs = voxel_size;
-    prm.inv_vs = (float)(1.0 / (double)voxel_size);
-    prm.huber = huber_delta;
-    prm.damping = damping;
-    prm.lam_scale = damping / 6.0;
+    // the tracking kernel reads v_s, 1 / v_s, the Huber threshold and the damping; the fusion-only
+    // fields take the library's defaults (T = 5 v_s, eps = v_s, 75 degrees), as gsdf_create would
+    const Params prm = make_params(voxel_size, 5.0f * voxel_size, voxel_size, huber_delta, 0.25881904f, damping);
     Scratch sc = {};
     sc.accum = scratch;
     sc.counter = (unsigned int*)(scratch + kAccumWords);

@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -415,20 +416,44 @@ class RoomSequence:
     truncation: float
 
 
+class _SingleThreadedChildren:
+    """Within the block, processes started inherit single-threaded BLAS / OpenMP settings, so that
+    a pool of one process per core does not start one thread per core in each of them."""
+
+    VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __enter__(self):
+        self.saved = {k: os.environ.get(k) for k in self.VARS}
+        for k in self.VARS:
+            os.environ[k] = "1"
+
+    def __exit__(self, *a):
+        for k, v in self.saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
 def room_sequence(seed: int = 2, n_frames: int = 100, cam: Camera = KINECT_640, voxel_size=0.01,
-                  noise=True, frames_per_segment=25, processes: int = 1) -> RoomSequence:
+                  noise=True, frames_per_segment=25, processes: int = 1,
+                  conditioned_horizon: int | None = None) -> RoomSequence:
     """Room scene, smooth trajectory and noisy depth frames (sigma = 0.0012 z^2).  `processes` > 1
     ray-casts the frames in a spawned pool; the noise is drawn afterwards in frame order, so the
-    frames do not depend on it."""
+    frames do not depend on it.  With conditioned_horizon the trajectory is re-drawn until every
+    view over that many frames is well-conditioned (conditioned_trajectory)."""
     scene = make_room(seed)
-    poses = room_trajectory(scene, n_frames, seed, frames_per_segment)
+    if conditioned_horizon is None:
+        poses = room_trajectory(scene, n_frames, seed, frames_per_segment)
+    else:
+        poses = conditioned_trajectory(scene, cam, n_frames, seed, frames_per_segment, conditioned_horizon)
     rng = np.random.default_rng(seed + 104729)
     if processes > 1:
         import concurrent.futures as cf
         import functools
         import multiprocessing as mp
 
-        with cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+        with _SingleThreadedChildren(), cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
             clean = list(ex.map(functools.partial(render_depth, scene, cam), poses, chunksize=4))
     else:
         clean = [render_depth(scene, cam, T) for T in poses]
@@ -507,21 +532,27 @@ MIN_OBSERVABILITY = 0.03
 MAX_TURN_DEG = 1.5
 
 
-def batch_room_trajectory(scene: RoomScene, cam: Camera, n_frames: int, seed: int) -> list:
-    """A room trajectory of the batch workload: drawn as room_trajectory does, and re-drawn with
-    the next seed until, over the first max(n_frames, BATCH_HORIZON) frames, the camera turns at
-    most MAX_TURN_DEG per frame and every view has view_observability >= MIN_OBSERVABILITY.
-    The check covers a fixed horizon, so a sequence's first frames do not depend on its length."""
-    horizon = max(n_frames, BATCH_HORIZON)
+def conditioned_trajectory(scene: RoomScene, cam: Camera, n_frames: int, seed: int, frames_per_segment=25,
+                           horizon: int = BATCH_HORIZON) -> list:
+    """A room trajectory drawn as room_trajectory does, and re-drawn with the next seed until, over
+    the first max(n_frames, horizon) frames, the camera turns at most MAX_TURN_DEG per frame and
+    every view has view_observability >= MIN_OBSERVABILITY.  The check covers a fixed horizon, so a
+    sequence's first frames do not depend on its length."""
+    h = max(n_frames, horizon)
     poses = None
     for attempt in range(256):
-        poses = room_trajectory(scene, horizon, seed + 1_000_003 * attempt)
+        poses = room_trajectory(scene, h, seed + 1_000_003 * attempt, frames_per_segment)
         if max_turn_deg(poses) <= MAX_TURN_DEG and all(
                 view_observability(scene, cam, T) >= MIN_OBSERVABILITY for T in poses):
             break
     else:
         raise RuntimeError(f"no well-conditioned trajectory found for seed {seed}")
     return poses[:n_frames]
+
+
+def batch_room_trajectory(scene: RoomScene, cam: Camera, n_frames: int, seed: int) -> list:
+    """A room trajectory of the batch workload: conditioned_trajectory over BATCH_HORIZON frames."""
+    return conditioned_trajectory(scene, cam, n_frames, seed)
 
 
 def batch_scene(index: int, n_frames: int, seed: int = 5) -> BatchScene:
@@ -554,7 +585,7 @@ def batch_scenes(n_scenes: int, n_frames: int, seed: int = 5, processes: int = 1
         import functools
         import multiprocessing as mp
 
-        with cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+        with _SingleThreadedChildren(), cf.ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
             return list(ex.map(functools.partial(batch_scene, n_frames=n_frames, seed=seed), range(n_scenes)))
     return [batch_scene(i, n_frames, seed) for i in range(n_scenes)]
 

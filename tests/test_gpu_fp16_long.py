@@ -11,7 +11,10 @@ against its own map.  Bars at each checkpoint c:
     error enters the next average with weight W / W' <= 1, so after c frames
     |psi - psi_oracle| <= c 2^-11 T (plus FP32 noise);
   * ghat: its mean error stays below 1e-3 (the per-frame half-precision level); the maximum is
-    printed with the other figures.
+    printed with the other figures;
+  * the track is kept: the position stays within 5 cm of the truth (the sequence is drawn so that
+    every view constrains all six degrees of freedom; a frame-to-model tracker without loop
+    closure drifts with the path length, and a lost track jumps by tens of centimetres).
 """
 import numpy as np
 import pytest
@@ -41,7 +44,8 @@ def G():
 
 @pytest.fixture(scope="module")
 def seq():
-    return I.room_sequence(seed=2, n_frames=FRAMES + 1, voxel_size=VOXEL, frames_per_segment=75, processes=8)
+    return I.room_sequence(seed=2, n_frames=FRAMES + 1, voxel_size=VOXEL, frames_per_segment=75, processes=8,
+                           conditioned_horizon=FRAMES + 1)
 
 
 def test_fp16_300_frames_against_oracle(G, seq):
@@ -84,5 +88,6 @@ def test_fp16_300_frames_against_oracle(G, seq):
                   f"mean {dpsi.mean():.2e} (bound {f * 2**-11 * T_trunc:.2e}), |dghat| max {dg.max():.2e} "
                   f"mean {dg.mean():.2e}, position error vs truth {err:.2e} m")
             assert dpose < 1e-4, (f, dpose)
+            assert err < 0.05, (f, err)  # drifts with the path, but stays tracked
             assert dpsi.max() <= f * 2**-11 * T_trunc + 1e-6, f
             assert dg.mean() <= 1e-3, f

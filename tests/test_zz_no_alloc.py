@@ -54,11 +54,10 @@ def test_noalloc_track_step_matches_handle_path_twice():
         b = G.track_stats_from_bytes(stats[call].cpu().numpy())
         assert a.status == b.status == G.GSDF_OK
         assert a.n_valid == b.n_valid > 5000
-        d = np.sqrt(np.diag(np.array(a.H)[[0, 6, 11, 15, 18, 20]]))
-        H_a, H_b = np.array(a.H), np.array(b.H)
-        assert np.all(np.abs(H_a - H_b) <= 1e-5 * np.max(d) ** 2 + 1e-9)
-        assert np.allclose(a.b, b.b, rtol=1e-5, atol=1e-9)
-        assert np.abs(pose.cpu().numpy() - pose_ref.cpu().numpy()).max() < 1e-4
+        # the same kernel with the same grid over the same inputs, and grid sums that are exact in
+        # any order: the statistics (H, b, energy, counts, increment) and the pose agree bit for bit
+        assert bytes(stats_ref[call].cpu().numpy()) == bytes(stats[call].cpu().numpy()), call
+        assert np.array_equal(pose.cpu().numpy(), pose_ref.cpu().numpy()), call
     m.sync()
 
     # invalid arguments are rejected before anything is launched
