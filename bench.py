@@ -281,8 +281,8 @@ def forms_summary(forms):
             "ms_per_frame": {m: f[m]["ms_per_frame"] for m in ("fp32", "fp16")},
             "voxels": f["fp16"]["voxels"],
             "pose_error_m_at_300": {m: f[m]["pose_error_m"][last] for m in ("fp32", "fp16")},
-            "fp16_vs_fp32_at_300": {k: f["checkpoints"][last]["fields_fp16_vs_fp32"][k]
-                                    for k in ("max_dpsi", "max_dghat")},
+            "fp16_vs_fp32_at_300_same_poses": {k: f["checkpoints"][last]["fields_fp16_vs_fp32_same_poses"][k]
+                                               for k in ("max_dpsi", "mean_dpsi", "max_dghat", "mean_dghat")},
             "hbm_frac": {m: {k: {"per_access": f[m]["roofline"][k]["per_access"]["frac"],
                                  "compulsory": f[m]["roofline"][k]["compulsory"]["frac"]} for k in ("track", "fusion")}
                          for m in ("fp32", "fp16")}}
@@ -764,6 +764,7 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
     depths = torch.from_numpy(seq.depths).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     out, fields, poses_at = {}, {}, {}
+    track_fp32 = torch.zeros((FP16_FRAMES + 1, 4, 4), dtype=torch.float64, device=dev)  # the FP32 run's poses
     for mode in ("fp32", "fp16"):
         m = G.Map(G.make_config(FP16_VOXEL, hash_slots=FP16_SLOTS, fp16=(mode == "fp16"),
                                 max_touched_blocks=FP16_SLOTS // 2), stream)
@@ -789,6 +790,8 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
             ev.append(e)
             valid[f - 1] = tstats[GN_ITERS - 1].view(torch.int64)[28]  # n_valid of the last step
             visits[f - 1] = istats.view(torch.int64)[1]
+            if mode == "fp32":
+                track_fp32[f] = pose
             if f in FP16_CHECKS:  # untimed: pose and fields at the checkpoint
                 torch.cuda.synchronize(dev)
                 poses_at[mode][f] = pose.cpu().numpy()
@@ -845,10 +848,21 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
                 "max_dpsi": float(dpsi.max()), "mean_dpsi": float(dpsi.mean()), "dpsi": pct(dpsi),
                 "max_dghat": float(dg.max()), "mean_dghat": float(dg.mean()), "dghat": pct(dg)}
 
+    # untimed: the FP16 payload fused at the FP32 run's own poses, so that both maps take the same
+    # decisions and differ only by the payload's precision
+    same = {}
+    m = G.Map(G.make_config(FP16_VOXEL, hash_slots=FP16_SLOTS, fp16=True, max_touched_blocks=FP16_SLOTS // 2), stream)
+    track_fp32[0] = torch.from_numpy(np.ascontiguousarray(seq.poses[0])).to(dev)
+    for f in range(FP16_FRAMES + 1):
+        m.integrate(depths[f], K, track_fp32[f])
+        if f in FP16_CHECKS:
+            same[f] = field_diff(fields["fp32"][f], m.extract())
+    m.close()
     checks = {}
     for c in FP16_CHECKS:
         checks[str(c)] = {"pose_diff_fp16_vs_fp32": float(np.abs(poses_at["fp16"][c] - poses_at["fp32"][c]).max()),
-                          "fields_fp16_vs_fp32": field_diff(fields["fp32"][c], fields["fp16"][c])}
+                          "fields_fp16_vs_fp32": field_diff(fields["fp32"][c], fields["fp16"][c]),
+                          "fields_fp16_vs_fp32_same_poses": same[c]}
     return {
         "workload": f"hashed room at 4 mm voxels (T = 2 cm), 640x480, {FP16_FRAMES} frames at 0.5 cm/frame, "
                     f"{GN_ITERS} GN steps + fusion per frame, every frame timed, L2 flushed before each",
