@@ -1128,6 +1128,68 @@ def adjoint_form(G, torch, dev, stream, ks, hbm_peak):
     }
 
 
+def profile_case(case):
+    """Small standalone runs of single kernels' workloads, for ncu captures (not benchmark lines):
+    batchN / batchN_fp16: the first N scenes of the batch workload (rooms FP16 with _fp16), frame 0
+    fused at its true pose, autotuned, then 4 frames of gsdf_batch_frame (10 GN steps + fusion);
+    fp16_4mm: the 4 mm room fused with the FP16 payload at its true poses, 9 frames.  Prints the
+    event-timed milliseconds per call."""
+    import torch
+
+    from paper_2111_13652_gb300 import gsdf as G
+    from paper_2111_13652_gb300 import inputs as I
+
+    procs = max(1, min(16, os.cpu_count() or 1))
+    if case.startswith("batch"):
+        fp16 = case.endswith("_fp16")
+        n = int(case[len("batch"):].split("_")[0])
+        frames = 4
+        scenes = I.batch_scenes(n, frames + 1, processes=procs)
+        G.load_library()
+        dev = torch.device("cuda")
+        maps = []
+        for sc in scenes:
+            if sc.dense_dims is not None:
+                cfg = G.make_config(sc.voxel_size, dense_dims=sc.dense_dims, dense_origin=sc.dense_origin,
+                                    damping=sc.damping)
+            else:
+                cfg = G.make_config(sc.voxel_size, hash_slots=sc.hash_slots, damping=sc.damping, fp16=fp16,
+                                    max_touched_blocks=sc.hash_slots // 2)
+            maps.append(G.Map(cfg))
+        depths = [torch.from_numpy(sc.depths).to(dev) for sc in scenes]
+        poses = [torch.from_numpy(np.ascontiguousarray(sc.poses[0])).to(dev) for sc in scenes]
+        b = G.Batch(maps)
+        b.set_frames([d[0] for d in depths], [G.intrinsics(sc.cam) for sc in scenes], poses)
+        b.set_depth_stride([sc.cam.width * sc.cam.height for sc in scenes])
+        b.frame(0)
+        b.autotune()
+        calls = [lambda: b.frame(GN_ITERS)] * frames
+    elif case == "fp16_4mm":
+        frames = 9
+        seq = I.room_sequence(seed=SEED, n_frames=frames, voxel_size=FP16_VOXEL, frames_per_segment=75,
+                              processes=procs)
+        G.load_library()
+        dev = torch.device("cuda")
+        m = G.Map(G.make_config(FP16_VOXEL, hash_slots=FP16_SLOTS, fp16=True, max_touched_blocks=FP16_SLOTS // 2))
+        K = G.intrinsics(seq.cam)
+        depths = torch.from_numpy(seq.depths).to(dev)
+        poses = torch.from_numpy(np.stack(seq.poses)).to(dev)
+        calls = [(lambda f=f: m.integrate(depths[f], K, poses[f])) for f in range(frames)]
+    else:
+        raise SystemExit(f"unknown profile case {case}")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ts = []
+    for k, call in enumerate(calls):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    print(case, "ms per call:", " ".join(f"{a.elapsed_time(c):.3f}" for a, c in ts), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1141,7 +1203,13 @@ def main():
     ap.add_argument("--no-points-form", action="store_true")
     ap.add_argument("--no-trilinear-form", action="store_true")
     ap.add_argument("--no-ba-form", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    help="run one small standalone case for an ncu capture instead of the benchmark "
+                         "(batchN, batchN_fp16, fp16_4mm)")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -169,10 +169,13 @@ __global__ void batch_advance_kernel(SceneDesc* descs, int n) {
 }
 
 constexpr int kBatchIntThreads = 256;
+constexpr int kFusePx = 2048;  // pixels per fusion work item (8 per thread)
 
-__global__ void __launch_bounds__(kBatchIntThreads)
-batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int total_tiles, int tile_px,
-                       unsigned int* counters) {
+// Fusion cuts its own work items, smaller than tracking tiles (which the autotuner sizes for the
+// tracking step): item i is part i % split of tracking tile i / split, fuse_px pixels.
+__global__ void __launch_bounds__(kBatchIntThreads, 4)
+batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int total_items, int tile_px,
+                       int split, int fuse_px, unsigned int* counters) {
     __shared__ PoseF pose;
     __shared__ int s_item;
     __shared__ unsigned int s_rays, s_visits, s_new;
@@ -183,13 +186,14 @@ batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int
         }
         __syncthreads();
         const int item = s_item;
-        if (item >= total_tiles) break;
-        SceneDesc* d = descs + __ldg(tile_scene + item);
+        if (item >= total_items) break;
+        const int tile = item / split;
+        SceneDesc* d = descs + __ldg(tile_scene + tile);
         if (threadIdx.x < (int)(sizeof(PoseF) / sizeof(float)))
             reinterpret_cast<float*>(&pose)[threadIdx.x] = reinterpret_cast<const float*>(&d->pose32)[threadIdx.x];
-        const int lt = item - d->tile_begin;
-        const int p0 = lt * tile_px;
-        const int p1 = min(p0 + tile_px, d->n_px);
+        const int lt = tile - d->tile_begin;
+        const int p0 = min(lt * tile_px + (item - tile * split) * fuse_px, d->n_px);
+        const int p1 = min(p0 + fuse_px, d->n_px);
         const Params prm = d->prm;
         const Intr K = d->K;
         const float* depth = d->depth;
@@ -347,9 +351,12 @@ cudaError_t launch_batch_fusion(gsdf_batch* b, cudaStream_t st) {
     batch_prologue_kernel<<<pro, 128, 0, st>>>(b->d_desc, b->n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(b->total_tiles, 6 * b->num_sms));
-    batch_integrate_kernel<<<grid, kBatchIntThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles,
-                                                              b->tile_px, b->d_counters);
+    const int fuse_px = std::min(b->tile_px, kFusePx);
+    const int split = b->tile_px / fuse_px;  // tile sizes are powers of two
+    const int items = b->total_tiles * split;
+    const int grid = std::max(1, std::min(items, 6 * b->num_sms));
+    batch_integrate_kernel<<<grid, kBatchIntThreads, 0, st>>>(b->d_desc, b->d_tile_scene, items, b->tile_px, split,
+                                                              fuse_px, b->d_counters);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (b->n_fp16 > 0) {
@@ -582,7 +589,7 @@ gsdf_status gsdf_batch_autotune(gsdf_batch* b, int32_t* tile_px_out, int32_t* ct
             b->h_desc[s].pose = b->d_scratch_pose + 16 * s;
             b->h_desc[s].tstats = nullptr;
         }
-        const int tiles[] = {512, 1024, 2048, 4096, 8192};
+        const int tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
         const int ctas[] = {1, 2};
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaEventCreate(&e0);

@@ -16,7 +16,7 @@
 namespace gsdf {
 
 template <class Map>
-__global__ void __launch_bounds__(kIntThreads)
+__global__ void __launch_bounds__(kIntThreads, 4)
 integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
                  const double* __restrict__ T_wc, gsdf_integrate_stats* stats, Scratch sc) {
     __shared__ PoseF pose;
