@@ -32,6 +32,9 @@
 namespace gsdf {
 
 constexpr int kSceneDense = 0, kSceneHashed = 1, kSceneHashed16 = 2;
+// The persistent kernels are instantiated for the set of scene kinds a batch holds (bit k set when
+// kind k is present), so that each carries only the map code it needs.
+constexpr int kAllKinds = 7;
 
 struct SceneDesc {
     int kind;        // kSceneDense, kSceneHashed or kSceneHashed16
@@ -69,6 +72,7 @@ __device__ __forceinline__ void batch_exit(unsigned int* work, unsigned int* exi
     }
 }
 
+template <int KINDS>
 __global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
 batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int total_tiles, int tile_px,
                    unsigned int* counters) {
@@ -93,15 +97,16 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
         for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
         const int pix0 = p0 + threadIdx.x;
         const float d0 = pix0 < p1 ? __ldg(depth + pix0) : 0.0f;
-        if (d->kind == kSceneDense) {
+        const int kind = d->kind;
+        if ((KINDS & (1 << kSceneDense)) && kind == kSceneDense) {
             const DenseMap m = d->dm;
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
-        } else if (d->kind == kSceneHashed) {
+        } else if ((KINDS & (1 << kSceneHashed)) && kind == kSceneHashed) {
             const HashMap m = d->hm;
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
-        } else {
+        } else if ((KINDS & (1 << kSceneHashed16)) && kind == kSceneHashed16) {
             const HashMap16 m = d->hm16;
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
@@ -173,6 +178,7 @@ constexpr int kFusePx = 2048;  // pixels per fusion work item (8 per thread)
 
 // Fusion cuts its own work items, smaller than tracking tiles (which the autotuner sizes for the
 // tracking step): item i is part i % split of tracking tile i / split, fuse_px pixels.
+template <int KINDS>
 __global__ void __launch_bounds__(kBatchIntThreads, 4)
 batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int total_items, int tile_px,
                        int split, int fuse_px, unsigned int* counters) {
@@ -199,15 +205,16 @@ batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int
         const float* depth = d->depth;
         __syncthreads();
         unsigned int rays = 0, visits = 0;
-        if (d->kind == kSceneDense) {
+        const int kind = d->kind;
+        if ((KINDS & (1 << kSceneDense)) && kind == kSceneDense) {
             const DenseMap m = d->dm;
             for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
                 integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
-        } else if (d->kind == kSceneHashed) {
+        } else if ((KINDS & (1 << kSceneHashed)) && kind == kSceneHashed) {
             const HashMap m = d->hm;
             for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
                 integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
-        } else {
+        } else if ((KINDS & (1 << kSceneHashed16)) && kind == kSceneHashed16) {
             const HashMap16 m = d->hm16;
             for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
                 integrate_ray(m, depth, K, prm, pose, pix, d->err, &s_new, rays, visits);
@@ -254,6 +261,7 @@ struct gsdf_batch {
     double* d_scratch_pose = nullptr;  // autotuning works on copies of the poses
     int* d_fp16_scenes = nullptr;      // indices of the FP16 scenes
     int n_fp16 = 0;
+    int kinds = 0;                     // bit k set when a scene of kind k is present
     int* d_tile_scene = nullptr;
     int tile_cap = 0;
     int total_tiles = 0;
@@ -337,10 +345,29 @@ cudaError_t wait_desc(gsdf_batch* b) {
     return cudaEventSynchronize(b->desc_copied);
 }
 
+// the instantiation of a persistent kernel for a batch's set of scene kinds
+template <int K>
+void launch_track_for(gsdf_batch* b, int grid, cudaStream_t st) {
+    batch_track_kernel<K><<<grid, kTrackThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles, b->tile_px,
+                                                           b->d_counters);
+}
+template <int K>
+void launch_fusion_for(gsdf_batch* b, int grid, int items, int split, int fuse_px, cudaStream_t st) {
+    batch_integrate_kernel<K><<<grid, kBatchIntThreads, 0, st>>>(b->d_desc, b->d_tile_scene, items, b->tile_px,
+                                                                  split, fuse_px, b->d_counters);
+}
+
 cudaError_t launch_batch_track(gsdf_batch* b, cudaStream_t st) {
     const int grid = std::max(1, std::min(b->total_tiles, b->ctas_per_sm * b->num_sms));
-    batch_track_kernel<<<grid, kTrackThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles, b->tile_px,
-                                                        b->d_counters);
+    switch (b->kinds) {
+        case 1: launch_track_for<1>(b, grid, st); break;
+        case 2: launch_track_for<2>(b, grid, st); break;
+        case 3: launch_track_for<3>(b, grid, st); break;
+        case 4: launch_track_for<4>(b, grid, st); break;
+        case 5: launch_track_for<5>(b, grid, st); break;
+        case 6: launch_track_for<6>(b, grid, st); break;
+        default: launch_track_for<kAllKinds>(b, grid, st); break;
+    }
     return cudaGetLastError();
 }
 
@@ -355,8 +382,15 @@ cudaError_t launch_batch_fusion(gsdf_batch* b, cudaStream_t st) {
     const int split = b->tile_px / fuse_px;  // tile sizes are powers of two
     const int items = b->total_tiles * split;
     const int grid = std::max(1, std::min(items, 6 * b->num_sms));
-    batch_integrate_kernel<<<grid, kBatchIntThreads, 0, st>>>(b->d_desc, b->d_tile_scene, items, b->tile_px, split,
-                                                              fuse_px, b->d_counters);
+    switch (b->kinds) {
+        case 1: launch_fusion_for<1>(b, grid, items, split, fuse_px, st); break;
+        case 2: launch_fusion_for<2>(b, grid, items, split, fuse_px, st); break;
+        case 3: launch_fusion_for<3>(b, grid, items, split, fuse_px, st); break;
+        case 4: launch_fusion_for<4>(b, grid, items, split, fuse_px, st); break;
+        case 5: launch_fusion_for<5>(b, grid, items, split, fuse_px, st); break;
+        case 6: launch_fusion_for<6>(b, grid, items, split, fuse_px, st); break;
+        default: launch_fusion_for<kAllKinds>(b, grid, items, split, fuse_px, st); break;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (b->n_fp16 > 0) {
@@ -467,6 +501,7 @@ gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda
         memset(&d, 0, sizeof(d));
         const gsdf_handle* hh = handles[s];
         d.kind = !hh->hashed ? kSceneDense : (hh->fp16 ? kSceneHashed16 : kSceneHashed);
+        b->kinds |= 1 << d.kind;
         d.dm = hh->dm;
         d.hm = hh->hm;
         d.hm16 = hh->hm16;
