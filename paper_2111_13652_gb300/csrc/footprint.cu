@@ -54,11 +54,7 @@ template <class Inner>
 __global__ void fuse_footprint_kernel(MarkMap<Inner> map, const float* __restrict__ depth, Intr K, Params prm,
                                       const double* __restrict__ T_wc) {
     __shared__ PoseF pose;
-    if (threadIdx.x == 0) {
-        double T[16];
-        for (int i = 0; i < 16; ++i) T[i] = T_wc[i];
-        round_pose(T, pose);
-    }
+    if (threadIdx.x < 32) round_pose_warp(T_wc, pose);
     __syncthreads();
     unsigned int rays = 0, visits = 0, n_new = 0;
     int err = 0;
@@ -73,11 +69,7 @@ __global__ void track_footprint_kernel(Map map, unsigned int* vbits, unsigned in
                                        const float* __restrict__ depth, Intr K, Params prm,
                                        const double* __restrict__ T_wc) {
     __shared__ PoseF pose;
-    if (threadIdx.x == 0) {
-        double T[16];
-        for (int i = 0; i < 16; ++i) T[i] = T_wc[i];
-        round_pose(T, pose);
-    }
+    if (threadIdx.x < 32) round_pose_warp(T_wc, pose);
     __syncthreads();
     const int n_px = K.width * K.height;
     for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < n_px; pix += gridDim.x * blockDim.x) {

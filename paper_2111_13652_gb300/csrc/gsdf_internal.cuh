@@ -307,6 +307,28 @@ __device__ inline void round_pose(const double* T, PoseF& q) {
     }
 }
 
+// The same rounding by the 24 lanes of one warp, one output value each (R: lanes 0..8, R^T:
+// 9..17, t: 18..20, -R^T t: 21..23), with the operations and their order of round_pose: a block
+// then waits for a few FP64 operations instead of thirty in one thread.  Called by the whole
+// warp; the caller synchronises before reading q.
+__device__ __forceinline__ void round_pose_warp(const double* T, PoseF& q) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 9) {
+        q.R[lane] = __double2float_rn(T[4 * (lane / 3) + lane % 3]);
+    } else if (lane < 18) {
+        const int k = lane - 9, i = k / 3, j = k % 3;  // (R^T)_ij = R_ji
+        q.RT[k] = __double2float_rn(T[4 * j + i]);
+    } else if (lane < 21) {
+        q.t[lane - 18] = __double2float_rn(T[4 * (lane - 18) + 3]);
+    } else if (lane < 24) {
+        const int i = lane - 21;
+        double s = __dmul_rn(T[0 * 4 + i], T[3]);
+        s = __dadd_rn(s, __dmul_rn(T[1 * 4 + i], T[7]));
+        s = __dadd_rn(s, __dmul_rn(T[2 * 4 + i], T[11]));
+        q.tinv[i] = __double2float_rn(-s);
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // launchers (defined in the kernel translation units)
 // ------------------------------------------------------------------------------------------

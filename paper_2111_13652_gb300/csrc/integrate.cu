@@ -21,12 +21,8 @@ integrate_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm,
                  const double* __restrict__ T_wc, gsdf_integrate_stats* stats, Scratch sc) {
     __shared__ PoseF pose;
     __shared__ unsigned int s_rays, s_visits, s_new;
-    if (threadIdx.x == 0) {
-        double T[16];
-        for (int i = 0; i < 16; ++i) T[i] = T_wc[i];
-        round_pose(T, pose);
-        s_rays = s_visits = s_new = 0u;
-    }
+    if (threadIdx.x < 32) round_pose_warp(T_wc, pose);
+    if (threadIdx.x == 0) s_rays = s_visits = s_new = 0u;
     __syncthreads();
 
     const int n_px = K.width * K.height;

@@ -231,6 +231,36 @@ def test_frame_graph_matches_separate_calls(G, scenes):
     del depths_a
 
 
+def test_frame_graph_with_refilled_buffers(G, scenes):
+    """Stride 0: the depth pointers stay on fixed buffers that the caller refills on the batch's
+    stream between gsdf_batch_frame calls; the graph reads the refilled frames and gives the poses
+    and voxel sets of the strided walk over the same frames."""
+    maps_a = [_map(G, sc) for sc in scenes]
+    batch_a, depths_a, poses_a, _ = _frame_batch(G, scenes, maps_a)  # depths_a stays referenced
+    maps_b = [_map(G, sc) for sc in scenes]
+    batch_b = G.Batch(maps_b)
+    bufs = [_dev(sc.depths[0]) for sc in scenes]
+    poses_b = [_dev(sc.poses[0]) for sc in scenes]
+    batch_b.set_frames(bufs, [G.intrinsics(sc.cam) for sc in scenes], poses_b)
+    batch_b.set_depth_stride([0] * len(scenes))
+    for f in range(3):
+        if f > 0:
+            for s, sc in enumerate(scenes):
+                bufs[s].copy_(depths_a[s][f])
+        batch_a.frame(0 if f == 0 else 10)
+        batch_b.frame(0 if f == 0 else 10)
+    torch.cuda.synchronize()
+    for s, sc in enumerate(scenes):
+        a, b = poses_a[s].cpu().numpy(), poses_b[s].cpu().numpy()
+        tol = 0.1 * sc.voxel_size if sc.dense_dims is not None else 1e-5
+        assert np.abs(_observable(sc, a) - _observable(sc, b)).max() < tol, s
+    for m in maps_a + maps_b:
+        m.sync()
+    batch_a.close()
+    batch_b.close()
+    del depths_a
+
+
 def test_autotune_leaves_state_unchanged(G, scenes):
     batch_maps, _, batch, Ks = _setup(G, scenes)
     d0 = [_dev(sc.depths[0]) for sc in scenes]
