@@ -5,7 +5,7 @@ The GPU runs the whole SLAM loop (10 Gauss-Newton steps then fusion per frame) w
 payload.  The oracle fuses every frame at the GPU's tracked pose, so both maps see the same
 decisions; at frames 1, 10, 100 and 300 it also tracks the frame from the GPU's previous pose
 against its own map.  Bars at each checkpoint c:
-  * pose: the oracle's 10 steps land within 1e-4 of the GPU's (the north-star pose tolerance);
+  * pose: the oracle's 10 steps land within 1e-4 of the GPU's (the library's pose tolerance);
   * voxel set: identical (decided on the FP32 index path from the same poses);
   * psi: each frame's re-encode adds at most 2^-11 sigma_b <= 2^-11 T to a voxel, and an earlier
     error enters the next average with weight W / W' <= 1, so after c frames
