@@ -58,6 +58,19 @@ struct SceneDesc {
     PoseF pose32;  // the pose rounded once, written by the fusion prologue
 };
 
+// An FP16 map whose tracking lookup resolves the key before it loads the payload.  In the
+// persistent kernel, whose registers are capped for two CTAs of 512 threads per SM, loading the
+// home slot's payload and scale together with the key (HashMap16::lookup) costs more in spills
+// than it saves in latency.
+struct HashMap16TwoStep {
+    HashMap16 m;
+    __device__ __forceinline__ bool lookup(int mx, int my, int mz, float& psi, float& gx, float& gy,
+                                           float& gz) const {
+        const long long idx = m.find(mx, my, mz);
+        return idx >= 0 && m.voxel(idx, psi, gx, gy, gz);
+    }
+};
+
 // counters: [0] tracking work, [1] tracking exits, [2] fusion work, [3] fusion exits
 constexpr int kBatchCounters = 4;
 
@@ -107,7 +120,7 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
         } else if ((KINDS & (1 << kSceneHashed16)) && kind == kSceneHashed16) {
-            const HashMap16 m = d->hm16;
+            const HashMap16TwoStep m{d->hm16};
             for_pixels(depth, K.width, pix0, p1, blockDim.x, d0,
                        [&](float D, int, int u, int v) { track_pixel(m, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc); });
         }

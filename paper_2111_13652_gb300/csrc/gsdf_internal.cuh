@@ -95,6 +95,29 @@ __host__ __device__ inline unsigned long long mix64(unsigned long long k) {
     return k;
 }
 
+// Read-only loads issued where they are written (volatile asm is neither moved nor dropped), for
+// loads that are issued speculatively before the branch that decides whether they are used.
+__device__ __forceinline__ unsigned long long ld_nc_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_nc_f32(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_nc_f4(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ ushort4 ld_nc_h4(const ushort4* p) {
+    ushort4 v;
+    asm volatile("ld.global.nc.v4.u16 {%0, %1, %2, %3}, [%4];" : "=h"(v.x), "=h"(v.y), "=h"(v.z), "=h"(v.w) : "l"(p));
+    return v;
+}
+
 // ------------------------------------------------------------------------------------------
 // maps
 // ------------------------------------------------------------------------------------------
@@ -127,6 +150,11 @@ struct DenseMap {
         gy = a.z;
         gz = a.w;
         return true;
+    }
+    // find and voxel in one call (the tracking lookup of Eq. (taylor))
+    __device__ __forceinline__ bool lookup(int mx, int my, int mz, float& psi, float& gx, float& gy, float& gz) const {
+        const long long idx = find(mx, my, mz);
+        return idx >= 0 && voxel(idx, psi, gx, gy, gz);
     }
 };
 
@@ -195,6 +223,46 @@ struct HashMap {
         gz = a.w;
         return true;
     }
+    // Slot of `key` probing from slot s + 1 on (s itself held another key), or -1: the rest of
+    // find's probe sequence.
+    __device__ __forceinline__ long long probe_on(unsigned long long key, unsigned long long s) const {
+        for (int p = 1; p < max_probe; ++p) {
+            s = (s + 1) & mask;
+            const unsigned long long k = __ldg(keys + s);
+            if (k == key) return (long long)s;
+            if (k == kEmptyKey) return -1;
+        }
+        return -1;
+    }
+    // find and voxel in one call (the tracking lookup of Eq. (taylor)), with the same result.  The
+    // voxel's payload in the key's home slot is loaded together with that slot's key, so that a
+    // block found where it hashes to -- nearly every block at the tables' load factors -- costs one
+    // round trip to memory instead of two; the loads of a block found further on are repeated.
+    __device__ __forceinline__ bool lookup(int mx, int my, int mz, float& psi, float& gx, float& gy, float& gz) const {
+        const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
+        if (!block_in_range(bx, by, bz)) return false;
+        const unsigned long long key = pack_block(bx, by, bz);
+        const unsigned long long s = mix64(key) & mask;
+        const int local = (mx & 7) + 8 * (my & 7) + 64 * (mz & 7);
+        long long idx = (long long)s * kBlockVoxels + local;
+        const unsigned long long k = ld_nc_u64(keys + s);
+        float w = ld_nc_f32(W + idx);
+        float4 a = ld_nc_f4(A + idx);
+        if (k != key) {
+            if (k == kEmptyKey || max_probe < 2) return false;
+            const long long slot = probe_on(key, s);
+            if (slot < 0) return false;
+            idx = slot * kBlockVoxels + local;
+            w = __ldg(W + idx);
+            a = __ldg(A + idx);
+        }
+        if (!(w > 0.0f)) return false;
+        psi = __fdividef(a.x, w);
+        gx = a.y;
+        gy = a.z;
+        gz = a.w;
+        return true;
+    }
 };
 
 // FP16 payload on the same 8^3-block hash table.  Per voxel: half4 (psi / sigma_b, gbar) with
@@ -221,6 +289,35 @@ struct HashMap16 {
         const float w = __ldg(W + idx);
         const ushort4 h = __ldg(H + idx);  // issued with W and the block scale
         const float sb = __ldg(scale + (idx >> 9));
+        if (!(w > 0.0f)) return false;
+        psi = __half2float(__ushort_as_half(h.x)) * sb;
+        gx = __half2float(__ushort_as_half(h.y));
+        gy = __half2float(__ushort_as_half(h.z));
+        gz = __half2float(__ushort_as_half(h.w));
+        return true;
+    }
+    // find and voxel in one call, the home slot's payload and scale loaded with its key (as
+    // HashMap::lookup)
+    __device__ __forceinline__ bool lookup(int mx, int my, int mz, float& psi, float& gx, float& gy, float& gz) const {
+        const int bx = floor_div8(mx), by = floor_div8(my), bz = floor_div8(mz);
+        if (!block_in_range(bx, by, bz)) return false;
+        const unsigned long long key = pack_block(bx, by, bz);
+        const unsigned long long s = mix64(key) & base.mask;
+        const int local = (mx & 7) + 8 * (my & 7) + 64 * (mz & 7);
+        long long idx = (long long)s * kBlockVoxels + local;
+        const unsigned long long k = ld_nc_u64(base.keys + s);
+        float w = ld_nc_f32(W + idx);
+        ushort4 h = ld_nc_h4(H + idx);
+        float sb = ld_nc_f32(scale + s);
+        if (k != key) {
+            if (k == kEmptyKey || base.max_probe < 2) return false;
+            const long long slot = base.probe_on(key, s);
+            if (slot < 0) return false;
+            idx = slot * kBlockVoxels + local;
+            w = __ldg(W + idx);
+            h = __ldg(H + idx);
+            sb = __ldg(scale + slot);
+        }
         if (!(w > 0.0f)) return false;
         psi = __half2float(__ushort_as_half(h.x)) * sb;
         gx = __half2float(__ushort_as_half(h.y));

@@ -463,10 +463,8 @@ __device__ __forceinline__ void track_pixel(const Map& map, float D, const Intr&
     const int mx = round_voxel(P[0], prm.inv_vs);
     const int my = round_voxel(P[1], prm.inv_vs);
     const int mz = round_voxel(P[2], prm.inv_vs);
-    const long long idx = map.find(mx, my, mz);
-    if (idx < 0) return;
     float psi, g0, g1, g2;
-    if (!map.voxel(idx, psi, g0, g1, g2)) return;
+    if (!map.lookup(mx, my, mz, psi, g0, g1, g2)) return;
     const float gn2 = g0 * g0 + g1 * g1 + g2 * g2;
     if (!(gn2 > 0.0f)) return;
     const float inv_gn = rsqrtf(gn2);
