@@ -79,6 +79,16 @@ cudaError_t track_once(const gsdf_handle* h, const float* depth, const Intr& ki,
                         h->sc, h->num_sms, st);
 }
 
+// n Gauss-Newton steps: one launch for a single step, otherwise the chained launches (each step's
+// solve at the start of the next, then a final solve)
+cudaError_t track_n(const gsdf_handle* h, const float* depth, const Intr& ki, double* T_wc, gsdf_track_stats* stats,
+                    int n, cudaStream_t st) {
+    if (n == 1) return track_once(h, depth, ki, T_wc, stats, st);
+    return launch_track_chain(h->hashed || h->fp16 ? nullptr : &h->dm, h->hashed && !h->fp16 ? &h->hm : nullptr,
+                              h->fp16 ? &h->hm16 : nullptr, !h->fp16 && h->cfg.tracker == GSDF_TRACKER_TRILINEAR,
+                              depth, ki, h->prm, T_wc, stats, h->sc, h->num_sms, n, st);
+}
+
 gsdf_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return GSDF_OK;
     if (e == cudaErrorMemoryAllocation) return GSDF_ERR_OOM;
@@ -102,6 +112,7 @@ void free_handle(gsdf_handle* h) {
     cudaFree(h->hashed ? (void*)h->hm.A : (void*)h->dm.A);
     cudaFree(h->hashed ? (void*)h->hm.W : (void*)h->dm.W);
     cudaFree(h->sc.accum);
+    cudaFree(h->sc.chain);
     cudaFree(h->sc.counter);
     cudaFree(h->sc.err);
     cudaFree(h->sc.n_blocks);
@@ -183,6 +194,8 @@ gsdf_status gsdf_create(const gsdf_config* cfg, void* cuda_stream, gsdf_handle**
     h->sc.max_track_blocks = 2 * h->num_sms;
     if (e == cudaSuccess) e = cudaMalloc(&h->sc.accum, sizeof(unsigned long long) * kAccumWords);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->sc.accum, 0, sizeof(unsigned long long) * kAccumWords, h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&h->sc.chain, sizeof(unsigned long long) * kChainWords);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->sc.chain, 0, sizeof(unsigned long long) * kChainWords, h->stream);
     if (e == cudaSuccess) e = cudaMalloc(&h->sc.counter, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->sc.err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->sc.n_blocks, sizeof(unsigned int));
@@ -257,11 +270,8 @@ gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrin
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
     if (e != cudaSuccess) return from_cuda(e);
-    if (cs != cudaStreamCaptureStatusNone) {  // the caller is capturing: launch into its graph
-        for (int it = 0; it < n_iters && e == cudaSuccess; ++it)
-            e = track_once(h, depth_dev, ki, T_wc_dev, stats_dev ? stats_dev + it : nullptr, h->stream);
-        return from_cuda(e);
-    }
+    if (cs != cudaStreamCaptureStatusNone)  // the caller is capturing: launch into its graph
+        return from_cuda(track_n(h, depth_dev, ki, T_wc_dev, stats_dev, n_iters, h->stream));
     const bool same = h->track_exec && h->g_depth == depth_dev && h->g_pose == T_wc_dev && h->g_stats == stats_dev &&
                       h->g_iters == n_iters && memcmp(&h->g_K, K, sizeof(gsdf_intrinsics)) == 0;
     if (!same) {
@@ -272,9 +282,7 @@ gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrin
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return from_cuda(e);
-        cudaError_t le = cudaSuccess;
-        for (int it = 0; it < n_iters && le == cudaSuccess; ++it)
-            le = track_once(h, depth_dev, ki, T_wc_dev, stats_dev ? stats_dev + it : nullptr, h->capture_stream);
+        const cudaError_t le = track_n(h, depth_dev, ki, T_wc_dev, stats_dev, n_iters, h->capture_stream);
         e = cudaStreamEndCapture(h->capture_stream, &graph);
         if (le != cudaSuccess) e = le;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&h->track_exec, graph, 0);

@@ -436,10 +436,17 @@ struct Scratch {
     int* err;                   // sticky device error word
     unsigned int* n_blocks;     // number of allocated hash blocks
     int max_track_blocks;
+    unsigned long long* chain;  // [kChainWords] chained tracking steps: 3 accumulator sets, 2 poses
 };
 
 constexpr int kAccumCopies = 16;  // grid accumulators are replicated to spread atomic traffic
 constexpr int kAccumWords = kAccumCopies * 32 * 4;  // copies x 30 terms (21 H, 6 b, E, n_valid, n_huber, padded to 32) x 4 chunks
+constexpr int kChainWords = 3 * kAccumWords + 32;     // three accumulator sets, then two 16-double poses
+
+// n >= 2 Gauss-Newton steps as one chain of launches (track.cu; requires sc.chain)
+cudaError_t launch_track_chain(const DenseMap* dm, const HashMap* hm, const HashMap16* hm16, bool trilinear,
+                               const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                               gsdf_track_stats* stats, const Scratch& sc, int num_sms, int n, cudaStream_t st);
 
 cudaError_t launch_track(const DenseMap* dm, const HashMap* hm, const float* depth, const Intr& K,
                          const Params& prm, double* T_wc, gsdf_track_stats* stats,

@@ -39,6 +39,107 @@ track_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, doubl
     finish_scene(sh, sc.accum, sc.counter, prm, T_wc, stats);
 }
 
+// ------------------------------------------------------------------------------------------
+// Chained steps (gsdf_track with n >= 2): step j's normal equations are solved at the start of
+// step j + 1 by every block, from the exact sums step j left in memory, instead of by the last
+// block of step j after a ticket.  The kernel boundary is then the only grid-wide
+// synchronisation of a step: no fence, ticket or single-block tail, and no pose round trip
+// through memory before the pixels.  Each block computes the identical FP64 solve, exponential
+// and product (the same operations on the same exact sums), so poses and statistics are bit for
+// bit those of n single steps.
+//
+// Scratch (sc.chain): three accumulator sets and two pose buffers.  Step j adds into set j % 3
+// and reads set (j - 1) % 3; its block 0 writes the pose T_j into buffer j % 2, the statistics of
+// step j - 1, and zeroes set (j + 1) % 3, the one step j + 1 adds into (last read by step j - 1).
+// A final one-block kernel solves step n - 1, writes T_n and its statistics, and zeroes the sets
+// it read, so that all three are zero again for the next call.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long* chain_set(const Scratch& sc, int k) {
+    return sc.chain + (size_t)(k % 3) * kAccumWords;
+}
+__device__ __forceinline__ double* chain_pose(const Scratch& sc, int k) {
+    return reinterpret_cast<double*>(sc.chain + 3 * (size_t)kAccumWords) + 16 * (k & 1);
+}
+
+// Every block: the pose of step j into sh (FP64 in sh.Tsh, rounded in sh.Rt).  For j >= 1 it is
+// exp(xi_{j-1}^) T_{j-1}, solved here from set (j - 1) % 3; block 0 publishes it and the
+// statistics of step j - 1 and zeroes set (j + 1) % 3.  Ends with a block-wide barrier.
+__device__ __forceinline__ void chain_pose_in(TrackShared& sh, const double* T_wc, const Params& prm,
+                                              gsdf_track_stats* stats, const Scratch& sc, int j) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (j == 0) {
+        load_pose(sh, T_wc);
+        __syncthreads();
+        return;
+    }
+    const double* T_prev = j == 1 ? T_wc : chain_pose(sc, j - 1);
+    if (threadIdx.x < 16) sh.Tsh[threadIdx.x] = threadIdx.x < 12 ? __ldcg(T_prev + threadIdx.x) : 0.0;
+    gather_sums(sh, chain_set(sc, j + 2), false);  // set (j - 1) % 3
+    if (blockIdx.x == 0) {
+        unsigned long long* z = chain_set(sc, j + 1);
+        for (int i = threadIdx.x; i < kAccumWords; i += blockDim.x) z[i] = 0ull;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double tn;
+        solve_step_warp(sh, prm, (blockIdx.x == 0 && stats) ? stats + (j - 1) : nullptr, tn);
+        __syncwarp();
+        if (lane < 12) {
+            sh.Tsh[lane] = tn;
+            const int r = lane >> 2, c = lane & 3;
+            sh.Rt[c < 3 ? 3 * r + c : 9 + r] = __double2float_rn(tn);
+            if (blockIdx.x == 0) chain_pose(sc, j)[lane] = tn;
+        }
+    }
+    __syncthreads();
+}
+
+template <class Map, bool kTrilinear>
+__global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
+track_chain_kernel(Map map, const float* __restrict__ depth, Intr K, Params prm, const double* T_wc,
+                   gsdf_track_stats* stats, Scratch sc, int j) {
+    __shared__ TrackShared sh;
+    const int n_px = K.width * K.height;
+    const int pix0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const float d0 = pix0 < n_px ? __ldg(depth + pix0) : 0.0f;  // in flight with the sums and pose
+    chain_pose_in(sh, T_wc, prm, stats, sc, j);
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+    for_pixels(depth, K.width, pix0, n_px, gridDim.x * blockDim.x, d0, [&](float D, int, int u, int v) {
+        if (kTrilinear)
+            track_pixel_trilinear(map, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc);
+        else
+            track_pixel(map, D, K, sh.Rt, sh.Rt + 9, prm, u, v, acc);
+    });
+    const unsigned long long s = block_reduce_terms(sh, acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < 4 && lane < kTerms)
+        atomicAdd(chain_set(sc, j) + (blockIdx.x % kAccumCopies) * 128 + warp * 32 + lane, s);
+}
+
+// The last step's solve: T_n into T_wc, the statistics of step n - 1, sets (n - 1) % 3 and
+// (n + 1) % 3 zeroed.  One block of 128 threads.
+__global__ void __launch_bounds__(128) track_chain_final_kernel(Params prm, double* T_wc, gsdf_track_stats* stats,
+                                                                Scratch sc, int n) {
+    __shared__ TrackShared sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double* T_prev = chain_pose(sc, n - 1);
+    if (threadIdx.x < 16) sh.Tsh[threadIdx.x] = threadIdx.x < 12 ? __ldcg(T_prev + threadIdx.x) : 0.0;
+    gather_sums(sh, chain_set(sc, n - 1), true);
+    {
+        unsigned long long* z = chain_set(sc, n + 1);
+        for (int i = threadIdx.x; i < kAccumWords; i += blockDim.x) z[i] = 0ull;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double tn;
+        solve_step_warp(sh, prm, stats ? stats + (n - 1) : nullptr, tn);
+        if (lane < 12) T_wc[lane] = tn;
+    }
+}
+
 static long long track_blocks(const Intr& K, const Scratch& sc, int num_sms) {
     const long long n_px = (long long)K.width * K.height;
     long long blocks = (n_px + kTrackThreads - 1) / kTrackThreads;
@@ -54,6 +155,32 @@ static cudaError_t launch_step(const Map& map, const float* depth, const Intr& K
     const unsigned blocks = (unsigned)track_blocks(K, sc, num_sms);
     track_kernel<Map, kTri><<<blocks, kTrackThreads, 0, st>>>(map, depth, K, prm, T_wc, stats, sc);
     return cudaGetLastError();
+}
+
+template <class Map, bool kTri>
+static cudaError_t launch_chain(const Map& map, const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                               gsdf_track_stats* stats, const Scratch& sc, int num_sms, int n, cudaStream_t st) {
+    const unsigned blocks = (unsigned)track_blocks(K, sc, num_sms);
+    for (int j = 0; j < n; ++j) {
+        track_chain_kernel<Map, kTri><<<blocks, kTrackThreads, 0, st>>>(map, depth, K, prm, T_wc, stats, sc, j);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    track_chain_final_kernel<<<1, 128, 0, st>>>(prm, T_wc, stats, sc, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_track_chain(const DenseMap* dm, const HashMap* hm, const HashMap16* hm16, bool trilinear,
+                               const float* depth, const Intr& K, const Params& prm, double* T_wc,
+                               gsdf_track_stats* stats, const Scratch& sc, int num_sms, int n, cudaStream_t st) {
+    if (!sc.chain || n < 2) return cudaErrorInvalidValue;
+    if (hm16) return launch_chain<HashMap16, false>(*hm16, depth, K, prm, T_wc, stats, sc, num_sms, n, st);
+    if (trilinear) {
+        if (dm) return launch_chain<DenseMap, true>(*dm, depth, K, prm, T_wc, stats, sc, num_sms, n, st);
+        return launch_chain<HashMap, true>(*hm, depth, K, prm, T_wc, stats, sc, num_sms, n, st);
+    }
+    if (dm) return launch_chain<DenseMap, false>(*dm, depth, K, prm, T_wc, stats, sc, num_sms, n, st);
+    return launch_chain<HashMap, false>(*hm, depth, K, prm, T_wc, stats, sc, num_sms, n, st);
 }
 
 cudaError_t launch_track16(const HashMap16& hm, const float* depth, const Intr& K, const Params& prm, double* T_wc,

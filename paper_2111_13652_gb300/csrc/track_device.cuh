@@ -592,23 +592,22 @@ __device__ __forceinline__ bool add_partial_and_ticket(TrackShared& sh, unsigned
     return sh.flag != 0;
 }
 
-// Finish a scene's step (called by every thread of the block that took the last ticket): read
-// and clear the exact sums, solve in FP64, update the pose (loaded in sh.Tsh) and write the
-// statistics.  Ends with a block-wide barrier so the block may continue with other work.
-__device__ __forceinline__ void finish_scene(TrackShared& sh, unsigned long long* accum, unsigned int* counter,
-                                             const Params& prm, double* T_wc, gsdf_track_stats* stats) {
+// Warps 0..3 sum chunk (threadIdx.x / 32) of the 32 term slots of a scene's exact accumulators
+// over their copies (one coalesced load per copy), zero the copies if `clear`, and leave the chunk
+// sums in sh.tsum with the trace of H in the empty slot 30; they meet at a named barrier.  Other
+// warps do nothing.
+__device__ __forceinline__ void gather_sums(TrackShared& sh, unsigned long long* accum, bool clear) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     if (warp < 4) {
-        // warp q sums chunk q of the 32 term slots over the copies (one coalesced load per copy)
-        // and clears them for the next step
-        __threadfence();
         unsigned long long* col = accum + warp * 32 + lane;
         unsigned long long s[kAccumCopies];
 #pragma unroll
         for (int c = 0; c < kAccumCopies; ++c) s[c] = __ldcg(col + c * 128);
+        if (clear) {
 #pragma unroll
-        for (int c = 0; c < kAccumCopies; ++c) col[c * 128] = 0ull;
+            for (int c = 0; c < kAccumCopies; ++c) col[c * 128] = 0ull;
+        }
 #pragma unroll
         for (int h = kAccumCopies / 2; h > 0; h >>= 1)
 #pragma unroll
@@ -620,37 +619,60 @@ __device__ __forceinline__ void finish_scene(TrackShared& sh, unsigned long long
         sh.tsum[warp][lane] = lane == 30 ? tr : s[0];
         asm volatile("bar.sync 1, 128;" ::: "memory");
     }
+}
+
+// Warp 0, after gather_sums: the exact sums rounded once to FP64 (sh.total), the damped 6x6
+// solve, the exponential map and T' = exp(xi^) T with T in sh.Tsh; writes the statistics if
+// `stats`.  Returns whether the system was solved, and in lanes 0..11 the new pose entry
+// (lane = 4 row + column; unchanged from sh.Tsh when the system is degenerate).
+__device__ __forceinline__ bool solve_step_warp(TrackShared& sh, const Params& prm, gsdf_track_stats* stats,
+                                                double& tn) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    // lanes 0..29 the terms, lane 30 the trace: exact sums rounded once to FP64
+    unsigned long long lo, hi;
+    fx_join(sh.tsum[0][lane], sh.tsum[1][lane], sh.tsum[2][lane], sh.tsum[3][lane], lo, hi);
+    const double v = fx_to_double(lo, hi);
+    sh.total[lane] = v;
+    // the counts are whole numbers: their integer part is exact
+    const long long n_valid = (long long)__shfl_sync(full, hi, 28);
+    const long long n_huber = (long long)__shfl_sync(full, hi, 29);
+    const double tr = __shfl_sync(full, v, 30);
+    __syncwarp();
+    const double* total = sh.total;
+    const bool ok = solve6_warp(total, tr, prm.lam_scale, n_valid, sh.xi);
+    tn = lane < 12 ? sh.Tsh[lane] : 0.0;
+    if (ok) {
+        se3_exp_warp(sh.xi, sh.dT);
+        tn = compose_entry(sh.dT, sh.Tsh);  // T <- dT T, lanes 0..11
+    }
+    if (stats) {
+        if (lane < 21) stats->H[lane] = total[lane];
+        else if (lane < 27) stats->b[lane - 21] = total[lane];
+        if (lane < 6) stats->xi[lane] = ok ? sh.xi[lane] : 0.0;
+        if (lane == 0) {
+            stats->energy = total[27];
+            stats->n_valid = n_valid;
+            stats->n_huber = n_huber;
+            stats->status = ok ? (int)GSDF_OK : (int)GSDF_ERR_DEGENERATE;
+            stats->pad = 0;
+        }
+    }
+    return ok;
+}
+
+// Finish a scene's step (called by every thread of the block that took the last ticket): read
+// and clear the exact sums, solve in FP64, update the pose (loaded in sh.Tsh) and write the
+// statistics.  Ends with a block-wide barrier so the block may continue with other work.
+__device__ __forceinline__ void finish_scene(TrackShared& sh, unsigned long long* accum, unsigned int* counter,
+                                             const Params& prm, double* T_wc, gsdf_track_stats* stats) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < 4) __threadfence();  // the other blocks' additions, ordered before their tickets
+    gather_sums(sh, accum, true);
     if (warp == 0) {
-        // lanes 0..29 the terms, lane 30 the trace: exact sums rounded once to FP64
-        unsigned long long lo, hi;
-        fx_join(sh.tsum[0][lane], sh.tsum[1][lane], sh.tsum[2][lane], sh.tsum[3][lane], lo, hi);
-        const double v = fx_to_double(lo, hi);
-        sh.total[lane] = v;
-        // the counts are whole numbers: their integer part is exact
-        const long long n_valid = (long long)__shfl_sync(full, hi, 28);
-        const long long n_huber = (long long)__shfl_sync(full, hi, 29);
-        const double tr = __shfl_sync(full, v, 30);
-        __syncwarp();
-        const double* total = sh.total;
         if (lane == 0) *counter = 0u;
-        const bool ok = solve6_warp(total, tr, prm.lam_scale, n_valid, sh.xi);
-        if (ok) {
-            se3_exp_warp(sh.xi, sh.dT);
-            const double tn = compose_entry(sh.dT, sh.Tsh);  // T <- dT T, lanes 0..11
-            if (lane < 12) T_wc[lane] = tn;
-        }
-        if (stats) {
-            if (lane < 21) stats->H[lane] = total[lane];
-            else if (lane < 27) stats->b[lane - 21] = total[lane];
-            if (lane < 6) stats->xi[lane] = ok ? sh.xi[lane] : 0.0;
-            if (lane == 0) {
-                stats->energy = total[27];
-                stats->n_valid = n_valid;
-                stats->n_huber = n_huber;
-                stats->status = ok ? (int)GSDF_OK : (int)GSDF_ERR_DEGENERATE;
-                stats->pad = 0;
-            }
-        }
+        double tn;
+        if (solve_step_warp(sh, prm, stats, tn) && lane < 12) T_wc[lane] = tn;
     }
     __syncthreads();
 }
