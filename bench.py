@@ -271,8 +271,8 @@ def forms_summary(forms):
             "max_pose_error_in_voxels": {k: b["pose_accuracy"][k]["max_in_voxels"]
                                          for k in ("batched", "batched_fp16", "plain")},
             "accuracy_gate": b["pose_accuracy"]["gate_all_scenes_within_2_voxels"],
-            "hbm_frac": {m: {k: {"per_access": sp[m][k]["per_access"]["frac"],
-                                 "compulsory": sp[m][k]["compulsory"]["frac"]} for k in ("track", "fusion")}
+            "hbm_frac": {m: {k: {kk: sp[m][k][kk]["frac"] for kk in ("per_access", "usable_px", "compulsory")
+                                 if kk in sp[m][k]} for k in ("track", "fusion")}
                          for m in sp}}
     f = forms.get("fp16_payload_4mm")
     if f:
@@ -283,8 +283,8 @@ def forms_summary(forms):
             "pose_error_m_at_300": {m: f[m]["pose_error_m"][last] for m in ("fp32", "fp16")},
             "fp16_vs_fp32_at_300_same_poses": {k: f["checkpoints"][last]["fields_fp16_vs_fp32_same_poses"][k]
                                                for k in ("max_dpsi", "mean_dpsi", "max_dghat", "mean_dghat")},
-            "hbm_frac": {m: {k: {"per_access": f[m]["roofline"][k]["per_access"]["frac"],
-                                 "compulsory": f[m]["roofline"][k]["compulsory"]["frac"]} for k in ("track", "fusion")}
+            "hbm_frac": {m: {k: {kk: f[m]["roofline"][k][kk]["frac"] for kk in ("per_access", "usable_px", "compulsory")
+                                 if kk in f[m]["roofline"][k]} for k in ("track", "fusion")}
                          for m in ("fp32", "fp16")}}
     a = forms.get("adjoint_10_keyframes")
     if a:
@@ -457,8 +457,12 @@ def gpu_arm(args):
     visits_total = float(r["visits"].sum())
     # roofline of the two kernels; the dominant one (larger share of step time) is reported
     hbm, hbm_kind = measured_hbm_peak()
-    track_b = track_bytes("f32", H * W, r["n_valid"])  # per launch (per access)
-    track_gbs = float(track_b.sum() / (r["track_ms"].sum() / 1e3) / 1e9)  # 10 launches per interval
+    # tracking: nominal per-access bytes (40 B per pixel) for `achieved`; the implementation's own
+    # per-access count (usable pixels only, its 8 B key) and the compulsory bytes beside it
+    track_s = r["track_ms"].sum() / 1e3
+    track_nom_gbs = float(track_bytes_nominal("f32", H * W) * GN_ITERS * args.steps / track_s / 1e9)
+    track_b = track_bytes("f32", H * W, r["n_valid"])  # per launch (per access, usable pixels)
+    track_gbs = float(track_b.sum() / track_s / 1e9)  # 10 launches per interval
     int_b = fuse_bytes("f32", H * W, r["visits"])
     int_gbs = float(int_b.sum() / (r["int_ms"].sum() / 1e3) / 1e9)
     step_s = float(r["track_ms"].mean()) / 1e3 / GN_ITERS
@@ -468,13 +472,16 @@ def gpu_arm(args):
     if share_int >= share_track:
         dom, ach, traffic = "integrate_kernel", int_gbs, profiled_traffic("integrate_kernel")
     else:
-        dom, ach, traffic = "track_chain_kernel", track_gbs, profiled_traffic("track_chain_kernel")
+        dom, ach, traffic = "track_chain_kernel", track_nom_gbs, profiled_traffic("track_chain_kernel")
     roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "kernel": dom, "peak_source": hbm_kind,
-            "bytes": "per access (algorithmic): tracking 4 B of depth per pixel + 28 B (8 B key probe + 20 B "
-                     "payload) per usable pixel; fusion 4 B per pixel + 48 B (key + 20 B read-modify-write) per "
-                     "ray-voxel update",
-            "kernels": {"track_chain_kernel": {"GBs": track_gbs, "share": share_track,
+            "bytes": "per access (algorithmic): tracking 40 B per pixel (4 B depth + 20 B payload + 16 B hash "
+                     "slot, every pixel, no reuse); fusion 4 B per pixel + 48 B (key + 20 B read-modify-write) "
+                     "per ray-voxel update",
+            "kernels": {"track_chain_kernel": {"GBs": track_nom_gbs, "share": share_track,
+                                         "usable_px": {"GBs": track_gbs, "frac": track_gbs / hbm,
+                                                       "bytes": "4 B per pixel + 28 B (8 B key + 20 B payload) "
+                                                                "per usable pixel"},
                                          "us_per_launch": 1e6 * step_s,
                                          "launches": f"{GN_ITERS} chained steps and one final solve per frame; "
                                                      f"time per Gauss-Newton step",
@@ -537,6 +544,17 @@ SLOT_B = {"dense": 0, "f32": 8, "f16": 8}       # the 8 B block key probed per l
 PAYLOAD_B = {"dense": 20, "f32": 20, "f16": 16}  # per lookup: float4 + W (FP16: half4 + W + block scale)
 VOXEL_B = {"dense": 20, "f32": 20, "f16": 12}    # per distinct voxel (FP16: half4 + W)
 BLOCK_B = {"dense": 0, "f32": 8, "f16": 12}      # per distinct block (key; FP16 also its scale)
+
+
+# Nominal per-access bytes of one tracking lookup per pixel, with no reuse and every pixel counted:
+# 4 B of depth, the payload (FP32 20 B; FP16 10 B: psi, gbar and W at 2 B each) and a 16 B hash
+# slot (key and block index; none for a dense grid).
+NOMINAL_PX_B = {"dense": 4 + 20, "f32": 4 + 20 + 16, "f16": 4 + 10 + 16}
+
+
+def track_bytes_nominal(kind, n_px):
+    """One tracking step, nominal per-access bytes: NOMINAL_PX_B per pixel of the frame."""
+    return NOMINAL_PX_B[kind] * n_px
 
 
 def track_bytes(kind, n_px, n_valid, vox=None, blocks=None):
@@ -695,6 +713,7 @@ def batch_form(G, torch, dev, stream, scenes, hbm):
         k_steps = BATCH_SPLIT_STEPS
         valid_mean = np.sum(np.reshape(valid, (k_steps, n)), axis=0) / k_steps
         visits_mean = np.sum(np.reshape(visits, (k_steps, n)), axis=0) / k_steps
+        tb_nom = sum(track_bytes_nominal(kd[s], n_px[s]) for s in range(n))
         tb_acc = sum(track_bytes(kd[s], n_px[s], valid_mean[s]) for s in range(n))
         tb_cmp = sum(track_bytes(kd[s], n_px[s], 0, *fp_t[s]) for s in range(n))
         fb_acc = sum(fuse_bytes(kd[s], n_px[s], visits_mean[s]) for s in range(n))
@@ -704,8 +723,9 @@ def batch_form(G, torch, dev, stream, scenes, hbm):
         fuse_s = t_fuse / k_steps
         split[mode] = {
             "track": {"kernel": "batch_track_kernel", "us_per_step": 1e6 * step_s,
-                      "bytes_per_step": {"per_access": tb_acc, "compulsory": tb_cmp},
-                      "per_access": roof(tb_acc, step_s, hbm), "compulsory": roof(tb_cmp, step_s, hbm),
+                      "bytes_per_step": {"per_access": tb_nom, "usable_px": tb_acc, "compulsory": tb_cmp},
+                      "per_access": roof(tb_nom, step_s, hbm), "usable_px": roof(tb_acc, step_s, hbm),
+                      "compulsory": roof(tb_cmp, step_s, hbm),
                       "distinct_voxels": int(sum(x[0] for x in fp_t)), "usable_px": float(np.sum(valid_mean))},
             "fusion": {"kernel": "batch_integrate_kernel" + (" + batch_list16/apply16" if fp16 else ""),
                        "us_per_frame": 1e6 * fuse_s,
@@ -812,6 +832,7 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
         sl = slice(FP16_FRAMES - 100, FP16_FRAMES)
         step_s = float(t_track[sl].mean()) / GN_ITERS
         fuse_s = float(t_fuse[sl].mean())
+        tb_nom = track_bytes_nominal(kind, H * W)
         tb_acc = track_bytes(kind, H * W, float(nv[sl].mean()))
         tb_cmp = track_bytes(kind, H * W, 0, *fp_t)
         fb_acc = fuse_bytes(kind, H * W, float(nvis[sl].mean())) + (fp16_apply_bytes(*fp_f) if kind == "f16" else 0)
@@ -826,7 +847,8 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
                              for c in FP16_CHECKS},
             "status": int(st),
             "roofline": {
-                "track": {"us_per_step": 1e6 * step_s, "per_access": roof(tb_acc, step_s, hbm),
+                "track": {"us_per_step": 1e6 * step_s, "per_access": roof(tb_nom, step_s, hbm),
+                          "usable_px": roof(tb_acc, step_s, hbm),
                           "compulsory": roof(tb_cmp, step_s, hbm), "distinct_voxels": fp_t[0]},
                 "fusion": {"us_per_frame": 1e6 * fuse_s, "per_access": roof(fb_acc, fuse_s, hbm),
                            "compulsory": roof(fb_cmp, fuse_s, hbm), "distinct_voxels": fp_f[0]},
