@@ -271,7 +271,7 @@ def forms_summary(forms):
             "max_pose_error_in_voxels": {k: b["pose_accuracy"][k]["max_in_voxels"]
                                          for k in ("batched", "batched_fp16", "plain")},
             "accuracy_gate": b["pose_accuracy"]["gate_all_scenes_within_2_voxels"],
-            "hbm_frac": {m: {k: {kk: sp[m][k][kk]["frac"] for kk in ("per_access", "usable_px", "compulsory")
+            "hbm_frac": {m: {k: {kk: sp[m][k][kk]["frac"] for kk in ("per_access", "per_access_usable", "compulsory")
                                  if kk in sp[m][k]} for k in ("track", "fusion")}
                          for m in sp}}
     f = forms.get("fp16_payload_4mm")
@@ -283,7 +283,7 @@ def forms_summary(forms):
             "pose_error_m_at_300": {m: f[m]["pose_error_m"][last] for m in ("fp32", "fp16")},
             "fp16_vs_fp32_at_300_same_poses": {k: f["checkpoints"][last]["fields_fp16_vs_fp32_same_poses"][k]
                                                for k in ("max_dpsi", "mean_dpsi", "max_dghat", "mean_dghat")},
-            "hbm_frac": {m: {k: {kk: f[m]["roofline"][k][kk]["frac"] for kk in ("per_access", "usable_px", "compulsory")
+            "hbm_frac": {m: {k: {kk: f[m]["roofline"][k][kk]["frac"] for kk in ("per_access", "per_access_usable", "compulsory")
                                  if kk in f[m]["roofline"][k]} for k in ("track", "fusion")}
                          for m in ("fp32", "fp16")}}
     a = forms.get("adjoint_10_keyframes")
@@ -479,7 +479,7 @@ def gpu_arm(args):
                      "slot, every pixel, no reuse); fusion 4 B per pixel + 48 B (key + 20 B read-modify-write) "
                      "per ray-voxel update",
             "kernels": {"track_chain_kernel": {"GBs": track_nom_gbs, "share": share_track,
-                                         "usable_px": {"GBs": track_gbs, "frac": track_gbs / hbm,
+                                         "per_access_usable": {"GBs": track_gbs, "frac": track_gbs / hbm,
                                                        "bytes": "4 B per pixel + 28 B (8 B key + 20 B payload) "
                                                                 "per usable pixel"},
                                          "us_per_launch": 1e6 * step_s,
@@ -723,8 +723,8 @@ def batch_form(G, torch, dev, stream, scenes, hbm):
         fuse_s = t_fuse / k_steps
         split[mode] = {
             "track": {"kernel": "batch_track_kernel", "us_per_step": 1e6 * step_s,
-                      "bytes_per_step": {"per_access": tb_nom, "usable_px": tb_acc, "compulsory": tb_cmp},
-                      "per_access": roof(tb_nom, step_s, hbm), "usable_px": roof(tb_acc, step_s, hbm),
+                      "bytes_per_step": {"per_access": tb_nom, "per_access_usable": tb_acc, "compulsory": tb_cmp},
+                      "per_access": roof(tb_nom, step_s, hbm), "per_access_usable": roof(tb_acc, step_s, hbm),
                       "compulsory": roof(tb_cmp, step_s, hbm),
                       "distinct_voxels": int(sum(x[0] for x in fp_t)), "usable_px": float(np.sum(valid_mean))},
             "fusion": {"kernel": "batch_integrate_kernel" + (" + batch_list16/apply16" if fp16 else ""),
@@ -848,7 +848,7 @@ def fp16_form(G, torch, dev, stream, seq, hbm):
             "status": int(st),
             "roofline": {
                 "track": {"us_per_step": 1e6 * step_s, "per_access": roof(tb_nom, step_s, hbm),
-                          "usable_px": roof(tb_acc, step_s, hbm),
+                          "per_access_usable": roof(tb_acc, step_s, hbm),
                           "compulsory": roof(tb_cmp, step_s, hbm), "distinct_voxels": fp_t[0]},
                 "fusion": {"us_per_frame": 1e6 * fuse_s, "per_access": roof(fb_acc, fuse_s, hbm),
                            "compulsory": roof(fb_cmp, fuse_s, hbm), "distinct_voxels": fp_f[0]},
