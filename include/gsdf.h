@@ -212,14 +212,19 @@ gsdf_status gsdf_integrate(gsdf_handle* h, const float* depth_dev, const gsdf_in
 gsdf_status gsdf_track_step(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
                             double* T_wc_dev, gsdf_track_stats* stats_dev);
 
-/* n_iters consecutive Gauss-Newton steps, each exactly gsdf_track_step, in one call.
+/* n_iters consecutive Gauss-Newton steps, each exactly gsdf_track_step, in one call: the poses
+ * and statistics equal those of n_iters gsdf_track_step calls bit for bit.
  * stats_dev: NULL or a device array of n_iters gsdf_track_stats (entry k describes step k).
- * Unless the handle's stream is being captured by the caller (then the kernels are simply
- * launched into the caller's capture), the n_iters launches are recorded once into a CUDA graph
- * that is replayed while (depth_dev, *K, T_wc_dev, stats_dev, n_iters) stay the same; a call
- * with other arguments records a new graph (host-side cost, no device allocation by the
+ * With n_iters >= 2 the steps are chained: launch j first solves step j - 1's normal equations
+ * (in every thread block, from the exact sums step j - 1 left in the handle's scratch) and then
+ * tracks at the new pose, and one more launch solves the last step; the pose in T_wc_dev is
+ * written by that last launch.  Unless the handle's stream is being captured by the caller (then
+ * the kernels are simply launched into the caller's capture), the launches are recorded once into
+ * a CUDA graph that is replayed while (depth_dev, *K, T_wc_dev, stats_dev, n_iters) stay the same;
+ * a call with other arguments records a new graph (host-side cost, no device allocation by the
  * library).  Reusing one depth staging buffer and one stats buffer keeps every call a replay.
- * 1 <= n_iters <= 1024. */
+ * Calls on one handle are ordered by its stream; two calls of one handle must not run
+ * concurrently (they share the chain's scratch).  1 <= n_iters <= 1024. */
 gsdf_status gsdf_track(gsdf_handle* h, const float* depth_dev, const gsdf_intrinsics* K,
                        double* T_wc_dev, int32_t n_iters, gsdf_track_stats* stats_dev);
 
