@@ -44,9 +44,9 @@ def _room_map(G, room, **kw):
     return m, K, _dev(s.depths[3]), s.poses[2]
 
 
-def _sphere_map(G):
+def _sphere_map(G, **kw):
     c = I.dense_sphere_case(1)
-    m = G.Map(G.make_config(c.voxel_size, dense_dims=c.dims, dense_origin=c.origin, damping=1e-4))
+    m = G.Map(G.make_config(c.voxel_size, dense_dims=c.dims, dense_origin=c.origin, damping=1e-4, **kw))
     m.upload_dense(c.psi, c.grad, c.weight)
     return m, G.intrinsics(c.cam), _dev(c.depth), c.T_init
 
@@ -67,9 +67,10 @@ def _compare_chain_with_steps(G, m, K, depth, T0, n, calls=2):
     return p_chain.cpu().numpy(), [G.track_stats_from_bytes(x) for x in s_chain.cpu().numpy()]
 
 
+@pytest.mark.parametrize("tracker", [0, 1])
 @pytest.mark.parametrize("n", [2, 3, 10])
-def test_chain_equals_single_steps_dense(G, n):
-    m, K, depth, T0 = _sphere_map(G)
+def test_chain_equals_single_steps_dense(G, n, tracker):
+    m, K, depth, T0 = _sphere_map(G, tracker=tracker)
     _, st = _compare_chain_with_steps(G, m, K, depth, T0, n)
     assert all(s.status == G.GSDF_OK and s.n_valid > 5000 for s in st)
     m.close()
