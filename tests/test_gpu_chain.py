@@ -130,7 +130,8 @@ def test_chain_in_a_caller_captured_graph(G):
 
 def test_chain_full_size_against_oracle(G, room):
     """The benchmark's form: 10 frames fused at the true poses, then one gsdf_track call of 10
-    steps on the next frame; the poses of every step within 1e-4 of the oracle's (free-running)."""
+    steps on the next frame against 10 free-running oracle steps: the final poses within 1e-4, the
+    first step's usable-pixel count equal (both sides start at the same pose), every step solved."""
     s = room
     m = G.Map(G.make_config(s.voxel_size, hash_slots=1 << 17))
     om = O.OracleMap(O.params(s.voxel_size))
