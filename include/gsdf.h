@@ -348,12 +348,15 @@ gsdf_status gsdf_footprint(gsdf_handle* h, int32_t what, const float* depth_dev,
 
 /* ---------------------------------------------------------------------------------------------
  * Batches: many independent scenes (maps of any kind, payload and voxel size, frames of any
- * resolution) tracked and fused together in persistent launches (the tracking and fusion of
+ * resolution) tracked and fused together in batched launches (the tracking and fusion of
  * Sec. 5.3, run for many scenes at once).  Each Gauss-Newton step of every scene is one launch
- * over (scene, pixel-tile) items pulled from a device counter.  A scene's 6x6 solve runs in the
- * block that finishes its last tile while other blocks keep working, so the per-scene FP64 tail
- * overlaps the other scenes' pixel work.  Results per scene are those of gsdf_track_step /
- * gsdf_integrate on that scene's handle, up to FP32 summation order.
+ * over (scene, pixel-tile) items: for batches of up to 64 scenes and 2048 tiles a grid with one
+ * thread block per tile, whose per-scene constants travel in the launch's parameters; larger
+ * batches run a persistent kernel whose blocks pull items from a device counter.  A scene's 6x6
+ * solve runs in the block that finishes its last tile while other blocks keep working, so the
+ * per-scene FP64 tail overlaps the other scenes' pixel work.  Fusion is one persistent launch.
+ * Results per scene are those of gsdf_track_step / gsdf_integrate on that scene's handle, up to
+ * FP32 summation order.
  * ------------------------------------------------------------------------------------------- */
 typedef struct gsdf_batch gsdf_batch;
 
@@ -373,7 +376,7 @@ gsdf_status gsdf_batch_set_frames(gsdf_batch* b, const float* const* depth_dev, 
                                   double* const* T_wc_dev, gsdf_track_stats* track_stats_dev,
                                   gsdf_integrate_stats* integrate_stats_dev);
 
-/* One Gauss-Newton step of every scene (one persistent launch). */
+/* One Gauss-Newton step of every scene (one launch). */
 gsdf_status gsdf_batch_track_step(gsdf_batch* b);
 
 /* n_iters steps of every scene, recorded once into a CUDA graph and replayed while the tile

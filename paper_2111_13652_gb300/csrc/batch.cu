@@ -1,8 +1,11 @@
-// Batched tracking and fusion of many independent scenes in persistent launches.
+// Batched tracking and fusion of many independent scenes.
 //
 // A batch groups existing handles (dense, hashed FP32 or hashed FP16 maps of any voxel size) with
-// one depth frame per scene (any resolution).  The pixels of all scenes are cut into tiles;
-// resident CTAs pull (scene, tile) items from a device counter until none are left.
+// one depth frame per scene (any resolution).  The pixels of all scenes are cut into tiles.
+// Tracking runs one thread block per tile (batch_track_grid_kernel), with the scenes' fixed
+// values and the tile table in the launch's parameters, for batches within that table's limits;
+// larger batches, and fusion, run persistent kernels whose resident CTAs pull (scene, tile) items
+// from a device counter until none are left.
 //   * Tracking: a tile's 30 normal-equation terms go into its scene's exact fixed-point
 //     accumulators (the same accumulators and arithmetic as the single-scene kernel), and the
 //     CTA that takes a scene's last ticket solves that scene's 6x6 system and updates its pose
@@ -71,6 +74,30 @@ struct HashMap16TwoStep {
     }
 };
 
+// The per-scene values of a tracking step that stay fixed from frame to frame, and the scene of
+// every tile, passed to batch_track_grid_kernel as a kernel parameter.  Read from the launch's
+// parameter space with a block-uniform index, they need no registers across the pixel loop (the
+// persistent kernel holds its descriptor's values in registers capped at 64 per thread, and
+// spills).  The depth and pose pointers, which change between frames (on the device for strided
+// depths), stay in the descriptor table in global memory.
+struct SceneConst {
+    int kind, n_px, tile_begin, n_tiles;
+    Intr K;
+    Params prm;
+    DenseMap dm;
+    HashMap hm;
+    HashMap16 hm16;
+    unsigned long long* accum;
+    unsigned int* ticket;
+};
+constexpr int kParamScenes = 64;   // batches of up to this many scenes
+constexpr int kParamTiles = 2048;  // and tiles use the grid kernel
+struct BatchTrackParams {
+    SceneConst s[kParamScenes];
+    unsigned short tile_scene[kParamTiles];
+};
+static_assert(sizeof(BatchTrackParams) <= 32000, "kernel parameters are limited to 32,764 bytes");
+
 // counters: [0] tracking work, [1] tracking exits, [2] fusion work, [3] fusion exits
 constexpr int kBatchCounters = 4;
 
@@ -130,6 +157,44 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
         __syncthreads();
     }
     batch_exit(counters + 0, counters + 1);
+}
+
+// One Gauss-Newton step of every scene as a grid of tiles (block b tracks tile b), for batches
+// within the parameter table's limits; otherwise the persistent kernel above runs.  The same
+// per-tile work, reductions, tickets and finishing as batch_track_kernel.
+template <int KINDS>
+__global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
+batch_track_grid_kernel(const SceneDesc* descs, int tile_px, const __grid_constant__ BatchTrackParams p) {
+    __shared__ TrackShared sh;
+    const int item = blockIdx.x;
+    const int si = p.tile_scene[item];
+    const SceneConst& c = p.s[si];
+    const SceneDesc* d = descs + si;
+    load_pose(sh, d->pose);
+    const int lt = item - c.tile_begin;
+    const int p0 = lt * tile_px;
+    const int p1 = min(p0 + tile_px, c.n_px);
+    const float* depth = d->depth;
+    __syncthreads();
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+    const int pix0 = p0 + threadIdx.x;
+    const float d0 = pix0 < p1 ? __ldg(depth + pix0) : 0.0f;
+    const int kind = c.kind;
+    if ((KINDS & (1 << kSceneDense)) && kind == kSceneDense) {
+        for_pixels(depth, c.K.width, pix0, p1, blockDim.x, d0,
+                   [&](float D, int, int u, int v) { track_pixel(c.dm, D, c.K, sh.Rt, sh.Rt + 9, c.prm, u, v, acc); });
+    } else if ((KINDS & (1 << kSceneHashed)) && kind == kSceneHashed) {
+        for_pixels(depth, c.K.width, pix0, p1, blockDim.x, d0,
+                   [&](float D, int, int u, int v) { track_pixel(c.hm, D, c.K, sh.Rt, sh.Rt + 9, c.prm, u, v, acc); });
+    } else if ((KINDS & (1 << kSceneHashed16)) && kind == kSceneHashed16) {
+        for_pixels(depth, c.K.width, pix0, p1, blockDim.x, d0,
+                   [&](float D, int, int u, int v) { track_pixel(c.hm16, D, c.K, sh.Rt, sh.Rt + 9, c.prm, u, v, acc); });
+    }
+    const unsigned long long s = block_reduce_terms(sh, acc);
+    if (add_partial_and_ticket(sh, s, c.accum, c.ticket, lt, (unsigned)c.n_tiles))
+        finish_scene(sh, c.accum, c.ticket, c.prm, d->pose, d->tstats);
 }
 
 // Fusion prologue: round every pose once and clear the per-scene statistics.
@@ -289,8 +354,15 @@ struct gsdf_batch {
         int iters = 0, tiles = 0, tile_px = 0, ctas = 0;
         bool strided = false;
         const int* tile_ptr = nullptr;
+        unsigned params_version = 0;
     };
     Cached track_graph, frame_graph;
+    // parameters of batch_track_grid_kernel (valid when grid_ok), rebuilt whenever the descriptor
+    // table or the tiles change; graphs recorded with another version are recorded again
+    BatchTrackParams* params = nullptr;
+    std::vector<int> scene_of;  // scene of every tile
+    bool grid_ok = false;
+    unsigned params_version = 1;
 };
 
 namespace {
@@ -318,7 +390,36 @@ void free_batch(gsdf_batch* b) {
     cudaFree(b->d_scratch_pose);
     cudaFree(b->d_fp16_scenes);
     cudaFree(b->d_tile_scene);
+    delete b->params;
     delete b;
+}
+
+// Rebuild the grid kernel's parameters from the host descriptor table and the tile table.
+void fill_params(gsdf_batch* b, const std::vector<int>& scene_of) {
+    b->grid_ok = b->n <= kParamScenes && b->total_tiles <= kParamTiles;
+    if (!b->grid_ok) return;
+    BatchTrackParams next;
+    memset(&next, 0, sizeof(next));
+    for (int s = 0; s < b->n; ++s) {
+        const SceneDesc& d = b->h_desc[s];
+        SceneConst& c = next.s[s];
+        c.kind = d.kind;
+        c.n_px = d.n_px;
+        c.tile_begin = d.tile_begin;
+        c.n_tiles = d.n_tiles;
+        c.K = d.K;
+        c.prm = d.prm;
+        c.dm = d.dm;
+        c.hm = d.hm;
+        c.hm16 = d.hm16;
+        c.accum = d.accum;
+        c.ticket = d.ticket;
+    }
+    for (int t = 0; t < b->total_tiles; ++t) next.tile_scene[t] = (unsigned short)scene_of[t];
+    if (memcmp(&next, b->params, sizeof(next)) != 0) {
+        memcpy(b->params, &next, sizeof(next));
+        ++b->params_version;
+    }
 }
 
 // (Re)build the tile table for the current frame sizes and tile size; host-synchronous (only when
@@ -341,10 +442,13 @@ cudaError_t build_tiles(gsdf_batch* b) {
         if (e != cudaSuccess) return e;
         b->tile_cap = t;
     }
+    b->scene_of = scene_of;
+    fill_params(b, scene_of);
     return cudaMemcpy(b->d_tile_scene, scene_of.data(), sizeof(int) * (size_t)t, cudaMemcpyHostToDevice);
 }
 
 cudaError_t upload_desc(gsdf_batch* b) {
+    fill_params(b, b->scene_of);
     cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(SceneDesc) * (size_t)b->n, cudaMemcpyHostToDevice,
                                     b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->desc_copied, b->stream);
@@ -361,6 +465,10 @@ cudaError_t wait_desc(gsdf_batch* b) {
 // the instantiation of a persistent kernel for a batch's set of scene kinds
 template <int K>
 void launch_track_for(gsdf_batch* b, int grid, cudaStream_t st) {
+    if (b->grid_ok) {
+        batch_track_grid_kernel<K><<<b->total_tiles, kTrackThreads, 0, st>>>(b->d_desc, b->tile_px, *b->params);
+        return;
+    }
     batch_track_kernel<K><<<grid, kTrackThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles, b->tile_px,
                                                            b->d_counters);
 }
@@ -444,7 +552,8 @@ cudaError_t replay(gsdf_batch* b, gsdf_batch::Cached& g, int iters, F&& record) 
     if (e != cudaSuccess) return e;
     if (cs != cudaStreamCaptureStatusNone) return record(b->stream);
     const bool same = g.exec && g.iters == iters && g.tiles == b->total_tiles && g.tile_px == b->tile_px &&
-                      g.ctas == b->ctas_per_sm && g.tile_ptr == b->d_tile_scene && g.strided == b->strided;
+                      g.ctas == b->ctas_per_sm && g.tile_ptr == b->d_tile_scene && g.strided == b->strided &&
+                      g.params_version == b->params_version;
     if (!same) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
@@ -468,6 +577,7 @@ cudaError_t replay(gsdf_batch* b, gsdf_batch::Cached& g, int iters, F&& record) 
         g.ctas = b->ctas_per_sm;
         g.tile_ptr = b->d_tile_scene;
         g.strided = b->strided;
+        g.params_version = b->params_version;
     }
     return cudaGraphLaunch(g.exec, b->stream);
 }
@@ -483,6 +593,11 @@ gsdf_status gsdf_batch_create(gsdf_handle* const* handles, int32_t n, void* cuda
         if (!handles[s] || handles[s]->cfg.tracker != GSDF_TRACKER_TAYLOR) return GSDF_ERR_INVALID_ARG;
     gsdf_batch* b = new (std::nothrow) gsdf_batch();
     if (!b) return GSDF_ERR_OOM;
+    b->params = new (std::nothrow) BatchTrackParams();
+    if (!b->params) {
+        delete b;
+        return GSDF_ERR_OOM;
+    }
     b->n = n;
     b->stream = (cudaStream_t)cuda_stream;
     b->h.assign(handles, handles + n);

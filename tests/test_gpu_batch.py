@@ -1,4 +1,4 @@
-"""Batched persistent launches (many scenes of uneven sizes) against per-scene calls and the oracle.
+"""Batched launches (many scenes of uneven sizes) against per-scene calls and the oracle.
 
 Eight scenes cycle through 160x120 .. 640x480 frames, dense 64^3 grids and hashed rooms, and
 1-4 cm voxels.  Fusion through the batch must give every scene the voxel set of a single-scene
@@ -276,4 +276,37 @@ def test_autotune_leaves_state_unchanged(G, scenes):
         after = m.extract()
         assert np.array_equal(after["m"], before[s]["m"]) and np.array_equal(after["w"], before[s]["w"])
         assert np.array_equal(poses[s].cpu().numpy(), p_before[s])
+    batch.close()
+
+
+def test_large_batch_takes_the_persistent_path(G, scenes):
+    """66 scenes, more than the tracking launch's parameter table holds (64), run on the persistent
+    work-queue kernel: every scene's batched Gauss-Newton step equals a single-scene step on the same
+    map from the same pose (counts exactly, normal equations within the FP32 summation bounds)."""
+    pick = [scenes[0], scenes[1]]  # a dense 64^3 sphere (160x120) and a hashed room (320x240)
+    big = [pick[s % 2] for s in range(66)]
+    maps = [_map(G, sc) for sc in big]
+    Ks = [G.intrinsics(sc.cam) for sc in big]
+    batch = G.Batch(maps)
+    d0 = [_dev(sc.depths[0]) for sc in big]
+    batch.set_frames(d0, Ks, [_dev(sc.poses[0]) for sc in big])
+    batch.integrate()
+    d1 = [_dev(sc.depths[1]) for sc in big]
+    pb = [_dev(sc.poses[0]) for sc in big]
+    tstats = torch.zeros((len(big), G.TRACK_STATS_BYTES), dtype=torch.uint8, device="cuda")
+    batch.set_frames(d1, Ks, pb, track_stats=tstats)
+    batch.track_step()
+    torch.cuda.synchronize()
+    for s, sc in enumerate(big):
+        ps = _dev(sc.poses[0])
+        st_single = maps[s].new_track_stats()
+        maps[s].track_step(d1[s], Ks[s], ps, st_single)
+        a = G.track_stats_from_bytes(tstats[s].cpu().numpy())
+        b = G.track_stats_from_bytes(st_single.cpu().numpy())
+        assert a.status == b.status == G.GSDF_OK
+        assert a.n_valid == b.n_valid > 100, s
+        assert_normal_equations_match(a, b)
+        assert np.abs(pb[s].cpu().numpy() - ps.cpu().numpy()).max() < 1e-5, s
+    for m in maps:
+        m.sync()
     batch.close()
