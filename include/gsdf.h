@@ -354,8 +354,8 @@ gsdf_status gsdf_footprint(gsdf_handle* h, int32_t what, const float* depth_dev,
  * thread block per tile, whose per-scene constants travel in the launch's parameters; larger
  * batches run a persistent kernel whose blocks pull items from a device counter.  A scene's 6x6
  * solve runs in the block that finishes its last tile while other blocks keep working, so the
- * per-scene FP64 tail overlaps the other scenes' pixel work.  Fusion is one persistent launch.
- * Results per scene are those of gsdf_track_step / gsdf_integrate on that scene's handle, up to
+ * per-scene FP64 tail overlaps the other scenes' pixel work.  Fusion runs the same way (a grid of
+ * work items, or a persistent launch for larger batches).  Results per scene are those of gsdf_track_step / gsdf_integrate on that scene's handle, up to
  * FP32 summation order.
  * ------------------------------------------------------------------------------------------- */
 typedef struct gsdf_batch gsdf_batch;
@@ -384,8 +384,8 @@ gsdf_status gsdf_batch_track_step(gsdf_batch* b);
  * gsdf_batch_set_frames).  1 <= n_iters <= 1024. */
 gsdf_status gsdf_batch_track(gsdf_batch* b, int32_t n_iters);
 
-/* Fuse every scene's frame at its current pose (prologue, one persistent launch, for FP16 scenes
- * one persistent apply pass, epilogue). */
+/* Fuse every scene's frame at its current pose (prologue, one fusion launch, for FP16 scenes one
+ * persistent apply pass, epilogue). */
 gsdf_status gsdf_batch_integrate(gsdf_batch* b);
 
 /* Per-scene depth strides for gsdf_batch_frame: stride[s] (host array of n, in floats) is added

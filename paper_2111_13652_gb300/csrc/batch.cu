@@ -2,9 +2,10 @@
 //
 // A batch groups existing handles (dense, hashed FP32 or hashed FP16 maps of any voxel size) with
 // one depth frame per scene (any resolution).  The pixels of all scenes are cut into tiles.
-// Tracking runs one thread block per tile (batch_track_grid_kernel), with the scenes' fixed
-// values and the tile table in the launch's parameters, for batches within that table's limits;
-// larger batches, and fusion, run persistent kernels whose resident CTAs pull (scene, tile) items
+// For batches within the limits of a parameter table (64 scenes, 2048 tiles), tracking runs one
+// thread block per tile and fusion one per fusion item (batch_track_grid_kernel,
+// batch_integrate_grid_kernel), with the scenes' fixed values and the tile table in the launch's
+// parameters; larger batches run persistent kernels whose resident CTAs pull (scene, tile) items
 // from a device counter until none are left.
 //   * Tracking: a tile's 30 normal-equation terms go into its scene's exact fixed-point
 //     accumulators (the same accumulators and arithmetic as the single-scene kernel), and the
@@ -89,6 +90,8 @@ struct SceneConst {
     HashMap16 hm16;
     unsigned long long* accum;
     unsigned int* ticket;
+    int* err;
+    unsigned int* n_blocks;
 };
 constexpr int kParamScenes = 64;   // batches of up to this many scenes
 constexpr int kParamTiles = 2048;  // and tiles use the grid kernel
@@ -319,6 +322,60 @@ batch_integrate_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int
     batch_exit(counters + 2, counters + 3);
 }
 
+// Fusion of every scene's frame as a grid of work items (block b fuses item b: part b % split of
+// tracking tile b / split), the scenes' fixed values read from the launch's parameters (as
+// batch_track_grid_kernel); the same per-item work as batch_integrate_kernel.
+template <int KINDS>
+__global__ void __launch_bounds__(kBatchIntThreads, 4)
+batch_integrate_grid_kernel(const SceneDesc* descs, int tile_px, int split, int fuse_px,
+                            const __grid_constant__ BatchTrackParams p) {
+    __shared__ PoseF pose;
+    __shared__ unsigned int s_rays, s_visits, s_new;
+    const int item = blockIdx.x;
+    const int tile = item / split;
+    const int si = p.tile_scene[tile];
+    const SceneConst& c = p.s[si];
+    const SceneDesc* d = descs + si;
+    if (threadIdx.x < (int)(sizeof(PoseF) / sizeof(float)))
+        reinterpret_cast<float*>(&pose)[threadIdx.x] = reinterpret_cast<const float*>(&d->pose32)[threadIdx.x];
+    if (threadIdx.x == 0) s_rays = s_visits = s_new = 0u;
+    const int lt = tile - c.tile_begin;
+    const int p0 = min(lt * tile_px + (item - tile * split) * fuse_px, c.n_px);
+    const int p1 = min(p0 + fuse_px, c.n_px);
+    const float* depth = d->depth;
+    __syncthreads();
+    unsigned int rays = 0, visits = 0;
+    const int kind = c.kind;
+    if ((KINDS & (1 << kSceneDense)) && kind == kSceneDense) {
+        for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+            integrate_ray(c.dm, depth, c.K, c.prm, pose, pix, c.err, &s_new, rays, visits);
+    } else if ((KINDS & (1 << kSceneHashed)) && kind == kSceneHashed) {
+        for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+            integrate_ray(c.hm, depth, c.K, c.prm, pose, pix, c.err, &s_new, rays, visits);
+    } else if ((KINDS & (1 << kSceneHashed16)) && kind == kSceneHashed16) {
+        for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x)
+            integrate_ray(c.hm16, depth, c.K, c.prm, pose, pix, c.err, &s_new, rays, visits);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rays += __shfl_xor_sync(0xffffffffu, rays, o);
+        visits += __shfl_xor_sync(0xffffffffu, visits, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_rays, rays);
+        atomicAdd(&s_visits, visits);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_new) atomicAdd(c.n_blocks, s_new);
+        gsdf_integrate_stats* is = d->istats;
+        if (is) {
+            atomicAdd((unsigned long long*)&is->n_rays, (unsigned long long)s_rays);
+            atomicAdd((unsigned long long*)&is->n_visits, (unsigned long long)s_visits);
+            atomicAdd((unsigned long long*)&is->n_blocks_new, (unsigned long long)s_new);
+        }
+    }
+}
+
 }  // namespace gsdf
 
 using namespace gsdf;
@@ -414,6 +471,8 @@ void fill_params(gsdf_batch* b, const std::vector<int>& scene_of) {
         c.hm16 = d.hm16;
         c.accum = d.accum;
         c.ticket = d.ticket;
+        c.err = d.err;
+        c.n_blocks = d.n_blocks;
     }
     for (int t = 0; t < b->total_tiles; ++t) next.tile_scene[t] = (unsigned short)scene_of[t];
     if (memcmp(&next, b->params, sizeof(next)) != 0) {
@@ -474,6 +533,11 @@ void launch_track_for(gsdf_batch* b, int grid, cudaStream_t st) {
 }
 template <int K>
 void launch_fusion_for(gsdf_batch* b, int grid, int items, int split, int fuse_px, cudaStream_t st) {
+    if (b->grid_ok) {
+        batch_integrate_grid_kernel<K><<<items, kBatchIntThreads, 0, st>>>(b->d_desc, b->tile_px, split, fuse_px,
+                                                                            *b->params);
+        return;
+    }
     batch_integrate_kernel<K><<<grid, kBatchIntThreads, 0, st>>>(b->d_desc, b->d_tile_scene, items, b->tile_px,
                                                                   split, fuse_px, b->d_counters);
 }
