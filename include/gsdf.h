@@ -350,7 +350,7 @@ gsdf_status gsdf_footprint(gsdf_handle* h, int32_t what, const float* depth_dev,
  * Batches: many independent scenes (maps of any kind, payload and voxel size, frames of any
  * resolution) tracked and fused together in batched launches (the tracking and fusion of
  * Sec. 5.3, run for many scenes at once).  Each Gauss-Newton step of every scene is one launch
- * over (scene, pixel-tile) items: for batches of up to 64 scenes and 2048 tiles a grid with one
+ * over (scene, pixel-tile) items: for batches of up to 64 scenes and 4096 tiles a grid with one
  * thread block per tile, whose per-scene constants travel in the launch's parameters; larger
  * batches run a persistent kernel whose blocks pull items from a device counter.  A scene's 6x6
  * solve runs in the block that finishes its last tile while other blocks keep working, so the

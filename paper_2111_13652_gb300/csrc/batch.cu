@@ -2,7 +2,7 @@
 //
 // A batch groups existing handles (dense, hashed FP32 or hashed FP16 maps of any voxel size) with
 // one depth frame per scene (any resolution).  The pixels of all scenes are cut into tiles.
-// For batches within the limits of a parameter table (64 scenes, 2048 tiles), tracking runs one
+// For batches within the limits of a parameter table (64 scenes, 4096 tiles), tracking runs one
 // thread block per tile and fusion one per fusion item (batch_track_grid_kernel,
 // batch_integrate_grid_kernel), with the scenes' fixed values and the tile table in the launch's
 // parameters; larger batches run persistent kernels whose resident CTAs pull (scene, tile) items
@@ -94,7 +94,7 @@ struct SceneConst {
     unsigned int* n_blocks;
 };
 constexpr int kParamScenes = 64;   // batches of up to this many scenes
-constexpr int kParamTiles = 2048;  // and tiles use the grid kernel
+constexpr int kParamTiles = 4096;  // and tiles use the grid kernels
 struct BatchTrackParams {
     SceneConst s[kParamScenes];
     unsigned short tile_scene[kParamTiles];

@@ -280,9 +280,10 @@ def test_autotune_leaves_state_unchanged(G, scenes):
 
 
 def test_large_batch_takes_the_persistent_path(G, scenes):
-    """66 scenes, more than the tracking launch's parameter table holds (64), run on the persistent
-    work-queue kernel: every scene's batched Gauss-Newton step equals a single-scene step on the same
-    map from the same pose (counts exactly, normal equations within the FP32 summation bounds)."""
+    """66 scenes, more than the launches' parameter table holds (64), run on the persistent
+    work-queue kernels: the batched fusion gives the voxel sets of single-scene fusion (fields within
+    1e-5), and every scene's batched Gauss-Newton step equals a single-scene step on the same map from
+    the same pose (counts exactly, normal equations within the FP32 summation bounds)."""
     pick = [scenes[0], scenes[1]]  # a dense 64^3 sphere (160x120) and a hashed room (320x240)
     big = [pick[s % 2] for s in range(66)]
     maps = [_map(G, sc) for sc in big]
@@ -291,6 +292,13 @@ def test_large_batch_takes_the_persistent_path(G, scenes):
     d0 = [_dev(sc.depths[0]) for sc in big]
     batch.set_frames(d0, Ks, [_dev(sc.poses[0]) for sc in big])
     batch.integrate()
+    for s in (0, 1, 64, 65):
+        ref = _map(G, big[s])
+        ref.integrate(d0[s], Ks[s], _dev(big[s].poses[0]))
+        a, b = _sorted(maps[s].extract()), _sorted(ref.extract())
+        assert len(a) > 1000 and np.array_equal(a["m"], b["m"]), s
+        assert np.max(np.abs(a["psi"] - b["psi"])) <= 1e-5, s
+        ref.close()
     d1 = [_dev(sc.depths[1]) for sc in big]
     pb = [_dev(sc.poses[0]) for sc in big]
     tstats = torch.zeros((len(big), G.TRACK_STATS_BYTES), dtype=torch.uint8, device="cuda")
