@@ -5,8 +5,9 @@
 // For batches within the limits of a parameter table (64 scenes, 4096 tiles), tracking runs one
 // thread block per tile and fusion one per fusion item (batch_track_grid_kernel,
 // batch_integrate_grid_kernel), with the scenes' fixed values and the tile table in the launch's
-// parameters; larger batches run persistent kernels whose resident CTAs pull (scene, tile) items
-// from a device counter until none are left.
+// parameters (only the depth pointers, which the device advances between frames, and the fusion
+// poses rounded on the device are read from the descriptor table); larger batches run persistent
+// kernels whose resident CTAs pull (scene, tile) items from a device counter until none are left.
 //   * Tracking: a tile's 30 normal-equation terms go into its scene's exact fixed-point
 //     accumulators (the same accumulators and arithmetic as the single-scene kernel), and the
 //     CTA that takes a scene's last ticket solves that scene's 6x6 system and updates its pose
@@ -92,6 +93,9 @@ struct SceneConst {
     unsigned int* ticket;
     int* err;
     unsigned int* n_blocks;
+    double* pose;  // the scene's pose (fixed pointer; its value is updated on the device)
+    gsdf_track_stats* tstats;
+    gsdf_integrate_stats* istats;
 };
 constexpr int kParamScenes = 64;   // batches of up to this many scenes
 constexpr int kParamTiles = 4096;  // and tiles use the grid kernels
@@ -173,7 +177,7 @@ batch_track_grid_kernel(const SceneDesc* descs, int tile_px, const __grid_consta
     const int si = p.tile_scene[item];
     const SceneConst& c = p.s[si];
     const SceneDesc* d = descs + si;
-    load_pose(sh, d->pose);
+    load_pose(sh, c.pose);
     const int lt = item - c.tile_begin;
     const int p0 = lt * tile_px;
     const int p1 = min(p0 + tile_px, c.n_px);
@@ -197,7 +201,7 @@ batch_track_grid_kernel(const SceneDesc* descs, int tile_px, const __grid_consta
     }
     const unsigned long long s = block_reduce_terms(sh, acc);
     if (add_partial_and_ticket(sh, s, c.accum, c.ticket, lt, (unsigned)c.n_tiles))
-        finish_scene(sh, c.accum, c.ticket, c.prm, d->pose, d->tstats);
+        finish_scene(sh, c.accum, c.ticket, c.prm, c.pose, c.tstats);
 }
 
 // Fusion prologue: round every pose once and clear the per-scene statistics.
@@ -367,7 +371,7 @@ batch_integrate_grid_kernel(const SceneDesc* descs, int tile_px, int split, int 
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_new) atomicAdd(c.n_blocks, s_new);
-        gsdf_integrate_stats* is = d->istats;
+        gsdf_integrate_stats* is = c.istats;
         if (is) {
             atomicAdd((unsigned long long*)&is->n_rays, (unsigned long long)s_rays);
             atomicAdd((unsigned long long*)&is->n_visits, (unsigned long long)s_visits);
@@ -473,6 +477,9 @@ void fill_params(gsdf_batch* b, const std::vector<int>& scene_of) {
         c.ticket = d.ticket;
         c.err = d.err;
         c.n_blocks = d.n_blocks;
+        c.pose = d.pose;
+        c.tstats = d.tstats;
+        c.istats = d.istats;
     }
     for (int t = 0; t < b->total_tiles; ++t) next.tile_scene[t] = (unsigned short)scene_of[t];
     if (memcmp(&next, b->params, sizeof(next)) != 0) {
