@@ -371,7 +371,8 @@ gsdf_status gsdf_batch_destroy(gsdf_batch* b);
  * n intrinsics; track_stats_dev / integrate_stats_dev: NULL or device arrays of n entries.  The
  * descriptor table is copied to the device on the batch's stream.  A change of any frame size
  * rebuilds the tile table (host-synchronous, and uses an autotuned tile size when one is cached for
- * that set of sizes). */
+ * that set of sizes; otherwise 2048-px tiles, doubled up to 16384 px while a batch of at most 64
+ * scenes would need more than 4096 tiles). */
 gsdf_status gsdf_batch_set_frames(gsdf_batch* b, const float* const* depth_dev, const gsdf_intrinsics* K,
                                   double* const* T_wc_dev, gsdf_track_stats* track_stats_dev,
                                   gsdf_integrate_stats* integrate_stats_dev);

@@ -80,8 +80,8 @@ struct HashMap16TwoStep {
 // every tile, passed to batch_track_grid_kernel as a kernel parameter.  Read from the launch's
 // parameter space with a block-uniform index, they need no registers across the pixel loop (the
 // persistent kernel holds its descriptor's values in registers capped at 64 per thread, and
-// spills).  The depth and pose pointers, which change between frames (on the device for strided
-// depths), stay in the descriptor table in global memory.
+// spills).  The depth pointers, which the device advances between frames, and the fusion's
+// rounded poses stay in the descriptor table in global memory.
 struct SceneConst {
     int kind, n_px, tile_begin, n_tiles;
     Intr K;
@@ -755,6 +755,17 @@ gsdf_status gsdf_batch_set_frames(gsdf_batch* b, const float* const* depth_dev, 
         if (it != b->tuned.end()) {
             b->tile_px = it->second.first;
             b->ctas_per_sm = it->second.second;
+        } else {
+            // untuned: 2048-px tiles, larger while the tiles would not fit the grid kernels' table
+            b->tile_px = 2048;
+            if (b->n <= kParamScenes) {
+                auto tiles = [&](int px) {
+                    long long t = 0;
+                    for (int q = 0; q < b->n; ++q) t += (b->n_px[q] + px - 1) / px;
+                    return t;
+                };
+                while (b->tile_px < 16384 && tiles(b->tile_px) > kParamTiles) b->tile_px *= 2;
+            }
         }
         e = build_tiles(b);
         if (e != cudaSuccess) return batch_status(e);
