@@ -2,9 +2,9 @@
 // (and its 2x2x2 Taylor upsampling) and the marching-cubes mesh in the same order, and checkpoint
 // loading.
 //
-// Hashed maps: the occupied slots' block keys are collected, sorted (bitonic sort in global
-// memory; keys are unique, so the order is total), counted, prefix-summed, and each block's
-// voxels with W > 0 are written in local-index order.  Dense maps are processed as chunks of
+// Hashed maps: the occupied slots' block keys are collected, sorted (a bitonic network whose steps
+// within 4096-key chunks run in shared memory; keys are unique, so the order is total), counted,
+// prefix-summed, and each block's voxels with W > 0 are written in local-index order.  Dense maps are processed as chunks of
 // 512 consecutive linear voxels.  Output order therefore never depends on insertion order.
 #include "gsdf_internal.cuh"
 
@@ -31,6 +31,52 @@ __global__ void bitonic_step_kernel(unsigned long long* a, long long n, long lon
             a[l] = x;
         }
     }
+}
+
+// The same bitonic network, its steps with j < kSortChunk run in shared memory: chunks of
+// kSortChunk consecutive elements are independent for those steps.  Each pair (i, i ^ j) is ordered
+// ascending when (i & k) == 0, descending otherwise, with i the element's global index.
+constexpr int kSortChunk = 4096;
+constexpr int kSortThreads = 1024;
+
+__device__ __forceinline__ void sort_pairs_shared(unsigned long long* c, long long base, long long k, long long j) {
+    for (int t = threadIdx.x; t < kSortChunk / 2; t += blockDim.x) {
+        const int lo = ((t & ~(int)(j - 1)) << 1) | (t & (int)(j - 1));
+        const int hi = lo | (int)j;
+        const unsigned long long x = c[lo], y = c[hi];
+        const bool up = ((base + lo) & k) == 0;
+        if ((x > y) == up) {
+            c[lo] = y;
+            c[hi] = x;
+        }
+    }
+}
+
+// Every chunk through all stages k = 2 .. kSortChunk (N a multiple of kSortChunk).
+__global__ void __launch_bounds__(kSortThreads) bitonic_chunks_kernel(unsigned long long* a) {
+    __shared__ unsigned long long c[kSortChunk];
+    const long long base = (long long)blockIdx.x * kSortChunk;
+    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) c[i] = a[base + i];
+    __syncthreads();
+    for (long long k = 2; k <= kSortChunk; k <<= 1)
+        for (long long j = k >> 1; j > 0; j >>= 1) {
+            sort_pairs_shared(c, base, k, j);
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) a[base + i] = c[i];
+}
+
+// Stage k > kSortChunk, its steps j = kSortChunk / 2 .. 1, for every chunk.
+__global__ void __launch_bounds__(kSortThreads) bitonic_merge_chunks_kernel(unsigned long long* a, long long k) {
+    __shared__ unsigned long long c[kSortChunk];
+    const long long base = (long long)blockIdx.x * kSortChunk;
+    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) c[i] = a[base + i];
+    __syncthreads();
+    for (long long j = kSortChunk / 2; j > 0; j >>= 1) {
+        sort_pairs_shared(c, base, k, j);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) a[base + i] = c[i];
 }
 
 // Per chunk (hashed: sorted block i; dense: linear chunk i) the voxel base index and the number
@@ -241,16 +287,25 @@ static cudaError_t sorted_block_keys(const HashMap& hm, long long n_slots, cudaS
     unsigned int n_keys = 0;
     GSDF_CK(cudaMemcpyAsync(&n_keys, cnt.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     GSDF_CK(cudaStreamSynchronize(st));
-    const long long N = next_pow2(n_keys > 0 ? n_keys : 1);
+    // padded to a power of two no smaller than one shared-memory chunk
+    const long long N = next_pow2(n_keys > kSortChunk ? n_keys : kSortChunk);
     GSDF_CK(keys.alloc((size_t)N));
     GSDF_CK(cudaMemsetAsync(keys.p, 0xFF, sizeof(unsigned long long) * (size_t)N, st));
     if (n_keys)
         GSDF_CK(cudaMemcpyAsync(keys.p, tmp.p, sizeof(unsigned long long) * n_keys, cudaMemcpyDeviceToDevice, st));
-    for (long long k = 2; k <= N; k <<= 1)
-        for (long long j = k >> 1; j > 0; j >>= 1) {
+    // stages up to one chunk in shared memory; each larger stage: its steps j >= kSortChunk in
+    // global memory, the rest in shared memory
+    const unsigned chunks = (unsigned)(N / kSortChunk);
+    bitonic_chunks_kernel<<<chunks, kSortThreads, 0, st>>>(keys.p);
+    GSDF_CK(cudaGetLastError());
+    for (long long k = 2 * (long long)kSortChunk; k <= N; k <<= 1) {
+        for (long long j = k >> 1; j >= kSortChunk; j >>= 1) {
             bitonic_step_kernel<<<grid, 256, 0, st>>>(keys.p, N, j, k);
             GSDF_CK(cudaGetLastError());
         }
+        bitonic_merge_chunks_kernel<<<chunks, kSortThreads, 0, st>>>(keys.p, k);
+        GSDF_CK(cudaGetLastError());
+    }
     GSDF_CK(cudaStreamSynchronize(st));
     *n_keys_out = n_keys;
     return cudaSuccess;

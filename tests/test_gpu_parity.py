@@ -387,6 +387,28 @@ def test_extract_load_roundtrip(G, room):
     assert m2.num_blocks() == m.num_blocks()
 
 
+def test_extraction_order_is_canonical_for_many_blocks(G, room):
+    """Ten frames fused at 5 mm (more than 4096 blocks, so the block-key sort crosses several
+    shared-memory chunks): the extracted voxels come in ascending block order (x, then y, then z of
+    the block) and, within a block, ascending local index, whatever the table size that held them."""
+    s = room
+    K = G.intrinsics(s.cam)
+    outs = []
+    for slots in (1 << 17, 1 << 16):
+        m = _hash_map(G, 0.005, slots=slots)
+        for f in range(10):
+            m.integrate(_dev(s.depths[f]), K, _dev(s.poses[f]))
+        assert m.num_blocks() > 4096
+        outs.append(m.extract())
+        m.close()
+    a, b = outs
+    assert np.array_equal(a["m"], b["m"])
+    blk = np.floor_divide(a["m"], 8).astype(np.int64)
+    loc = (a["m"][:, 0] & 7) + 8 * (a["m"][:, 1] & 7) + 64 * (a["m"][:, 2] & 7)
+    key = ((blk[:, 0] + (1 << 20)) << 42) | ((blk[:, 1] + (1 << 20)) << 21) | (blk[:, 2] + (1 << 20))
+    assert np.all((key[1:] > key[:-1]) | ((key[1:] == key[:-1]) & (loc[1:] > loc[:-1])))
+
+
 def test_capacity_exhaustion_is_reported(G, room):
     """A table far too small fills up: the frame is partially fused, the sticky error word
     reports GSDF_ERR_CAPACITY, and the handle keeps working."""
