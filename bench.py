@@ -1155,7 +1155,9 @@ def adjoint_form(G, torch, dev, stream, ks, hbm_peak):
 def profile_case(case):
     """Small standalone runs of single kernels' workloads, for ncu captures (not benchmark lines):
     batchN / batchN_fp16: the first N scenes of the batch workload (rooms FP16 with _fp16), frame 0
-    fused at its true pose, autotuned, then 4 frames of gsdf_batch_frame (10 GN steps + fusion);
+    fused at its true pose, autotuned (not with a _fixed suffix: the default tile choice, so that a
+    capture does not depend on timings taken under the profiler), then 4 frames of gsdf_batch_frame
+    (10 GN steps + fusion);
     fp16_4mm: the 4 mm room fused with the FP16 payload at its true poses, 9 frames.  Prints the
     event-timed milliseconds per call."""
     import torch
@@ -1165,7 +1167,8 @@ def profile_case(case):
 
     procs = max(1, min(16, os.cpu_count() or 1))
     if case.startswith("batch"):
-        fp16 = case.endswith("_fp16")
+        fixed = case.endswith("_fixed")
+        fp16 = "_fp16" in case
         n = int(case[len("batch"):].split("_")[0])
         frames = 4
         scenes = I.batch_scenes(n, frames + 1, processes=procs)
@@ -1186,7 +1189,8 @@ def profile_case(case):
         b.set_frames([d[0] for d in depths], [G.intrinsics(sc.cam) for sc in scenes], poses)
         b.set_depth_stride([sc.cam.width * sc.cam.height for sc in scenes])
         b.frame(0)
-        b.autotune()
+        if not fixed:
+            b.autotune()
         calls = [lambda: b.frame(GN_ITERS)] * frames
     elif case == "fp16_4mm":
         frames = 9
