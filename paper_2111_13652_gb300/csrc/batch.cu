@@ -169,8 +169,10 @@ batch_track_kernel(SceneDesc* descs, const int* __restrict__ tile_scene, int tot
 // One Gauss-Newton step of every scene as a grid of tiles (block b tracks tile b), for batches
 // within the parameter table's limits; otherwise the persistent kernel above runs.  The same
 // per-tile work, reductions, tickets and finishing as batch_track_kernel.
+constexpr int kGridTrackThreads = 256;  // threads per tile block of batch_track_grid_kernel
+
 template <int KINDS>
-__global__ void __launch_bounds__(kTrackThreads, kTrackBlocksPerSM)
+__global__ void __launch_bounds__(kGridTrackThreads, 2 * kTrackBlocksPerSM)
 batch_track_grid_kernel(const SceneDesc* descs, int tile_px, const __grid_constant__ BatchTrackParams p) {
     __shared__ TrackShared sh;
     const int item = blockIdx.x;
@@ -199,7 +201,7 @@ batch_track_grid_kernel(const SceneDesc* descs, int tile_px, const __grid_consta
         for_pixels(depth, c.K.width, pix0, p1, blockDim.x, d0,
                    [&](float D, int, int u, int v) { track_pixel(c.hm16, D, c.K, sh.Rt, sh.Rt + 9, c.prm, u, v, acc); });
     }
-    const unsigned long long s = block_reduce_terms(sh, acc);
+    const unsigned long long s = block_reduce_terms<kGridTrackThreads / 32>(sh, acc);
     if (add_partial_and_ticket(sh, s, c.accum, c.ticket, lt, (unsigned)c.n_tiles))
         finish_scene(sh, c.accum, c.ticket, c.prm, c.pose, c.tstats);
 }
@@ -532,7 +534,7 @@ cudaError_t wait_desc(gsdf_batch* b) {
 template <int K>
 void launch_track_for(gsdf_batch* b, int grid, cudaStream_t st) {
     if (b->grid_ok) {
-        batch_track_grid_kernel<K><<<b->total_tiles, kTrackThreads, 0, st>>>(b->d_desc, b->tile_px, *b->params);
+        batch_track_grid_kernel<K><<<b->total_tiles, kGridTrackThreads, 0, st>>>(b->d_desc, b->tile_px, *b->params);
         return;
     }
     batch_track_kernel<K><<<grid, kTrackThreads, 0, st>>>(b->d_desc, b->d_tile_scene, b->total_tiles, b->tile_px,

@@ -558,7 +558,10 @@ __device__ __forceinline__ void track_pixel_trilinear(const Map& map, float D, c
 // fixed-point chunks with integer instructions; warp q < 4 then sums chunk q of the 32 term
 // slots over the warps.  Returns, in threads 0..127, chunk threadIdx.x / 32 of the block sum of
 // term threadIdx.x % 32 (0 elsewhere).  All threads call it.
+// kWarps: the block's warps (4 <= kWarps <= kTrackWarps).
+template <int kWarps = kTrackWarps>
 __device__ __forceinline__ unsigned long long block_reduce_terms(TrackShared& sh, float (&acc)[32]) {
+    static_assert(kWarps >= 4 && kWarps <= kTrackWarps, "block size");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned c[4];
     fx_chunks(warp_reduce_scatter32(acc), c);
@@ -568,7 +571,7 @@ __device__ __forceinline__ unsigned long long block_reduce_terms(TrackShared& sh
     unsigned long long s = 0ull;
     if (warp < 4) {
 #pragma unroll
-        for (int w = 0; w < kTrackWarps; ++w) s += sh.wchunk[w][warp][lane];
+        for (int w = 0; w < kWarps; ++w) s += sh.wchunk[w][warp][lane];
     }
     return s;
 }
