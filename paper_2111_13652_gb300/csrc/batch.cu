@@ -261,7 +261,7 @@ __global__ void batch_advance_kernel(SceneDesc* descs, int n) {
 }
 
 constexpr int kBatchIntThreads = 256;
-constexpr int kFusePx = 2048;  // pixels per fusion work item (8 per thread)
+constexpr int kFusePx = 4096;  // pixels per fusion work item (16 per thread)
 
 // Fusion cuts its own work items, smaller than tracking tiles (which the autotuner sizes for the
 // tracking step): item i is part i % split of tracking tile i / split, fuse_px pixels.
